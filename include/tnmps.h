@@ -1,0 +1,225 @@
+/*
+ * tnmps.h -- C ABI of the GB300 (sm_103a) matrix-product-state circuit
+ * simulator: parameterised-circuit application and Pauli-sum energies.
+ *
+ * The operations follow arXiv:1807.07914 (McCaskey et al., "Validating
+ * Quantum-Classical Programming Models with Tensor Network Simulations"):
+ *   - a register of n qubits held as an MPS of n rank-3 tensors (Sec. IV,
+ *     ITensor MPS implementation), initialised to a product state;
+ *   - single-qubit gates contracted into site tensors and adjacent two-qubit
+ *     gates applied by contraction to a rank-4 tensor and an SVD with a
+ *     singular-value cutoff (Sec. II, Fig. "mpssvd"; Sec. IV); distant
+ *     pairs are joined by SWAP chains (Sec. IV);
+ *   - a parameterised circuit executed for runtime parameter values and the
+ *     expectation value of every Hamiltonian term per parameter value
+ *     (Sec. V.B, VQE), here E(theta) = sum_k c_k <psi(theta)|P_k|psi(theta)>.
+ *
+ * Conventions
+ *   - qubit q lives on MPS site q; bit q of a basis index is qubit q;
+ *   - rotations are R_sigma(a) = exp(-i a sigma / 2);
+ *   - CNOT: q0 is the control, q1 the target;
+ *   - Pauli codes: 1 = X, 2 = Y, 3 = Z.
+ *
+ * Memory ownership
+ *   - The library allocates no device memory. The caller passes a device
+ *     arena (sized by tnmps_state_bytes) to tnmps_init and a device
+ *     workspace (sized by tnmps_expect_workspace_bytes) to each expectation
+ *     call; both must stay valid while the context uses them. Pointers must
+ *     be 256-byte aligned.
+ *   - Host pointers passed in are read during the call only. Host outputs
+ *     are written before the call returns (those calls synchronise the
+ *     context's stream). Functions with the suffix _dev take device
+ *     pointers, enqueue work on the context's stream and return without
+ *     synchronising.
+ *
+ * Errors
+ *   - Every call returns a tnmps_status; no call aborts, exits or traps.
+ *     tnmps_last_error(ctx) describes the last failure. Device-side problems
+ *     (an SVD that did not converge within its sweep cap, NaN/Inf in the
+ *     state) are recorded in a device flag and reported by the next
+ *     synchronising call or by tnmps_check. After an error the state is
+ *     unspecified until tnmps_reset.
+ *
+ * Threading: a context is used by one host thread at a time.
+ */
+#ifndef TNMPS_H_INCLUDED
+#define TNMPS_H_INCLUDED
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tnmps_ctx tnmps_ctx;
+typedef struct tnmps_terms tnmps_terms;
+
+/* Arithmetic of the state and of the contractions. TNMPS_C128: complex128
+ * everywhere (the plain FP64 form). TNMPS_C64: complex64 storage and FP32
+ * contractions/rotations; the energy reduction stays FP64. */
+typedef enum { TNMPS_C128 = 0, TNMPS_C64 = 1 } tnmps_dtype;
+
+typedef enum {
+  TNMPS_OK = 0,
+  TNMPS_ERR_ARG = 1,            /* invalid argument or size                   */
+  TNMPS_ERR_NOMEM = 2,          /* caller-supplied arena/workspace too small  */
+  TNMPS_ERR_UNSUPPORTED = 3,    /* gate or configuration not supported        */
+  TNMPS_ERR_NOT_CONVERGED = 4,  /* Jacobi SVD hit its sweep cap               */
+  TNMPS_ERR_NUMERIC = 5,        /* NaN or Inf met in singular values/energies */
+  TNMPS_ERR_CUDA = 6,           /* a CUDA runtime call failed                 */
+  TNMPS_ERR_INJECTED = 7        /* host-side fault injection (tests only)     */
+} tnmps_status;
+
+/* Gate opcodes (a gate list is the flat form of the paper's IR tree). */
+typedef enum {
+  TNMPS_I = 0, TNMPS_X = 1, TNMPS_Y = 2, TNMPS_Z = 3, TNMPS_H = 4,
+  TNMPS_S = 5, TNMPS_SDG = 6, TNMPS_T = 7,
+  TNMPS_RX = 8, TNMPS_RY = 9, TNMPS_RZ = 10,
+  TNMPS_CNOT = 16, TNMPS_CZ = 17, TNMPS_SWAP = 18
+} tnmps_op;
+
+/* One gate. Rotation angle = angle + scale * theta[param] if param >= 0,
+ * else angle (the runtime parameter of Sec. V.B). q1 = -1 for 1q gates. */
+typedef struct {
+  int32_t op, q0, q1, param;
+  double angle, scale;
+} tnmps_gate;
+
+/* Counters accumulated since init/reset (for roofline accounting). */
+typedef struct {
+  uint64_t gates2q;          /* two-qubit gate applications, summed over states */
+  uint64_t gates2q_full;     /* ... of which with D_{l-1} = D_l = D_{l+1} = chi_max */
+  uint64_t jacobi_pair_rows; /* sum over Jacobi pair visits of the column length */
+  uint64_t jacobi_rotations; /* pair visits that rotated                       */
+  uint64_t jacobi_sweeps;    /* sweeps, summed over SVDs                       */
+  uint64_t svds;             /* SVDs run (states x gates)                      */
+  uint64_t env_updates;      /* transfer-matrix updates (nodes x states)       */
+  uint64_t env_flops;        /* algorithmic real flops of those updates        */
+  uint64_t jacobi_rot_rows;  /* sum over rotated pairs of the column length     */
+  uint64_t launches;         /* kernel launches issued by this context (host count) */
+} tnmps_stats;
+
+/* Kernel classes for event timing. */
+typedef enum {
+  TNMPS_PROF_THETA = 0,   /* two-site block contraction + gate (K2)            */
+  TNMPS_PROF_JACOBI = 1,  /* one-sided Jacobi SVD (K3)                          */
+  TNMPS_PROF_SPLIT = 2,   /* truncate, orthonormalise, split, normalise (K4)    */
+  TNMPS_PROF_MOVE = 3,    /* gauge moves, Householder QR/LQ (K7)                */
+  TNMPS_PROF_GATE1 = 4,   /* standalone single-qubit gates (K1)                 */
+  TNMPS_PROF_ENV = 5,     /* transfer-matrix environment updates (K5)           */
+  TNMPS_PROF_TERM = 6,    /* term values and energy reduction (K6)              */
+  TNMPS_PROF_NUM = 7
+} tnmps_prof_class;
+
+const char *tnmps_status_string(tnmps_status s);
+const char *tnmps_version(void);
+
+/* ---- context ------------------------------------------------------------
+ * Device bytes needed for `batch` states of n qubits with bond cap chi_max
+ * and up to max_params circuit parameters per state. 0 on bad arguments. */
+size_t tnmps_state_bytes(int n_qubits, int chi_max, tnmps_dtype dtype, int batch,
+                         int max_params);
+
+/* Create a context on the current CUDA device using `arena` (device memory,
+ * arena_bytes >= tnmps_state_bytes(...)). The state is |0...0> for every
+ * batch member (Sec. IV: product-state initialisation). Cutoff defaults to
+ * 1e-4 (Sec. IV default). 1 <= n_qubits <= 4096, 1 <= chi_max <= 256,
+ * batch >= 1. */
+tnmps_status tnmps_init(tnmps_ctx **out, int n_qubits, int chi_max, tnmps_dtype dtype,
+                        int batch, int max_params, void *arena, size_t arena_bytes);
+void tnmps_free(tnmps_ctx *ctx);
+
+/* Singular values sigma_i < eps * ||sigma||_2 are dropped (relative cutoff;
+ * the paper's epsilon, Sec. IV); at most chi_max are kept, at least one.
+ * The effective cutoff is max(eps, 8u) with u the unit roundoff of the
+ * dtype (2^-53 for TNMPS_C128, 2^-24 for TNMPS_C64): singular values at the
+ * SVD's rounding-noise floor are always dropped. */
+tnmps_status tnmps_set_cutoff(tnmps_ctx *ctx, double eps);
+/* CUDA stream (cudaStream_t) for all work of this context; NULL = default. */
+tnmps_status tnmps_set_stream(tnmps_ctx *ctx, void *stream);
+/* Back to |0...0> with zero discarded weight and zeroed counters. */
+tnmps_status tnmps_reset(tnmps_ctx *ctx);
+
+/* ---- circuits ------------------------------------------------------------
+ * Apply a gate list to every state. theta: host array [n_params] shared by
+ * all states. Two-qubit gates on distant qubits use SWAP chains. */
+tnmps_status tnmps_apply_circuit(tnmps_ctx *ctx, const tnmps_gate *gates, size_t n_gates,
+                                 const double *theta, size_t n_params);
+/* Same, one parameter row per state: thetas host array [batch][n_params]. */
+tnmps_status tnmps_apply_circuit_batched(tnmps_ctx *ctx, const tnmps_gate *gates,
+                                         size_t n_gates, const double *thetas,
+                                         size_t n_params);
+/* Same, thetas a device array [batch][n_params]; asynchronous. */
+tnmps_status tnmps_apply_circuit_batched_dev(tnmps_ctx *ctx, const tnmps_gate *gates,
+                                             size_t n_gates, const double *thetas_dev,
+                                             size_t n_params);
+
+/* ---- Pauli sums -----------------------------------------------------------
+ * A term set in CSR form: term k acts with paulis[j] on sites[j] for
+ * term_off[k] <= j < term_off[k+1]; coeffs[k] is real. A term with no sites
+ * is the identity. Sites within a term must be distinct and < n_qubits.
+ * The host builds the prefix trie of the terms once here; arrays are copied. */
+tnmps_status tnmps_terms_create(tnmps_terms **out, int n_qubits, const int32_t *term_off,
+                                const int32_t *sites, const uint8_t *paulis,
+                                const double *coeffs, size_t n_terms);
+void tnmps_terms_free(tnmps_terms *terms);
+/* Trie size: nodes (= transfer updates per state), depth, widest level. */
+tnmps_status tnmps_terms_info(const tnmps_terms *terms, int64_t *n_nodes, int32_t *depth,
+                              int64_t *max_level_nodes);
+/* Device workspace bytes for evaluating `terms` on ctx with states processed
+ * in chunks of theta_chunk (0 = the whole batch at once). */
+size_t tnmps_expect_workspace_bytes(const tnmps_ctx *ctx, const tnmps_terms *terms,
+                                    int theta_chunk);
+/* E[b] = sum_k c_k <psi_b|P_k|psi_b> for every state b (host outputs,
+ * energy[batch]; per_term[batch][n_terms] of Re<P_k> may be NULL). */
+tnmps_status tnmps_expect_pauli_sum(tnmps_ctx *ctx, const tnmps_terms *terms, void *ws,
+                                    size_t ws_bytes, double *energy, double *per_term);
+/* Same with device outputs; asynchronous. */
+tnmps_status tnmps_expect_pauli_sum_dev(tnmps_ctx *ctx, const tnmps_terms *terms, void *ws,
+                                        size_t ws_bytes, double *energy_dev,
+                                        double *per_term_dev);
+
+/* ---- inspection ------------------------------------------------------------ */
+/* Synchronise and report device-side error flags. */
+tnmps_status tnmps_check(tnmps_ctx *ctx);
+/* Bond dimensions: dims[batch][n_qubits - 1] (synchronises). */
+tnmps_status tnmps_get_bond_dims(tnmps_ctx *ctx, int32_t *dims);
+/* Cumulative discarded weight per state: w[batch] (synchronises). */
+tnmps_status tnmps_get_discarded_weight(tnmps_ctx *ctx, double *w);
+/* Copy site tensor `site` of state b to host as complex128 (re, im pairs),
+ * row-major (D_{site-1}, 2, D_site); `cap` = capacity in complex elements. */
+tnmps_status tnmps_get_site(tnmps_ctx *ctx, int b, int site, double *out, size_t cap,
+                            int32_t *dl, int32_t *dr);
+/* Orthogonality centre (site index) after the work enqueued so far. */
+int tnmps_get_centre(const tnmps_ctx *ctx);
+tnmps_status tnmps_get_stats(tnmps_ctx *ctx, tnmps_stats *out);
+/* Time the kernel classes in class_mask (bit i = tnmps_prof_class i) with
+ * CUDA events recorded on the context's stream around each launch group;
+ * totals are cleared. class_mask = 0 stops timing. */
+tnmps_status tnmps_profile(tnmps_ctx *ctx, uint32_t class_mask);
+/* Synchronise and return accumulated milliseconds and launch-group counts
+ * per class (arrays of TNMPS_PROF_NUM entries, either may be NULL). */
+tnmps_status tnmps_profile_read(tnmps_ctx *ctx, double *ms, uint64_t *count);
+const char *tnmps_last_error(const tnmps_ctx *ctx);
+
+/* ---- standalone kernels (unit parity) --------------------------------------
+ * One-sided Jacobi SVD (the gate step's SVD, Sec. IV) on `batch` column-major
+ * m x n matrices: a_dev points to batch*lda*n complex elements (complex128
+ * or complex64 per dtype; matrix b at a_dev + b*lda*n). On return the
+ * columns are mutually orthogonal (A V); sigma_dev[batch][n] receives the
+ * column norms (unsorted) and sweeps_dev[batch] the sweep counts.
+ * m <= 512, n <= 512, lda >= m. Asynchronous on `stream`. */
+tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, void *a_dev,
+                                  int lda, double *sigma_dev, int32_t *sweeps_dev,
+                                  int max_sweeps, void *stream);
+
+/* Host-side fault injection for error-path tests: the call number `nth`
+ * (counting from 1) of any state-changing entry point returns `status`
+ * before touching the device. nth = 0 disarms. */
+tnmps_status tnmps_debug_inject(tnmps_ctx *ctx, int nth, tnmps_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNMPS_H_INCLUDED */

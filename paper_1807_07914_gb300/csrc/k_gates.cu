@@ -1,0 +1,758 @@
+// Gate-step kernels of the MPS update (paper Sec. II Fig. "mpssvd" and Sec. IV):
+//   K2  two-site block  Theta[(a,s1),(s2,b)] = sum G[s1 s2, s1' s2'] (C_l B_{l+1})[(a,s1'),(s2',b)]
+//   K4  truncate + split: sigma, rank by the cutoff rule, A_l <- U_k,
+//       C_{l+1} <- U_k^H Theta / ||sigma_kept||
+//   K1  standalone single-qubit gate on a site tensor
+//   K7  gauge moves of the orthogonality centre (Householder QR / LQ)
+//
+// Gauge: mixed canonical form. A two-qubit gate on (l, l+1) is applied with
+// the centre on l; afterwards A_l is a left isometry (columns of U) and the
+// centre C_{l+1} = Sigma_k V_k^H sits on l+1.
+//
+// Layouts (complex, row-major): site i of state b is (D_{i-1}, 2, D_i) at
+// sites + b*state_elems + site_off[i]; the row index of (a, s) is 2a + s and
+// the column index of (s, c) is s*D + c. Theta is row-major (2 D_{l-1}) x
+// (2 D_{l+1}) in theta_buf; its column-major copy in w_buf is the Jacobi
+// input.
+#include "gates_dev.cuh"
+#include "gemm_tile.cuh"
+#include "tnmps_internal.h"
+
+cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap);
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ cx<R> *site_ptr(const StateView &v, int b, int i) {
+  return reinterpret_cast<cx<R> *>(v.sites) + (int64_t)b * v.state_elems + v.site_off[i];
+}
+__device__ __forceinline__ int dimv(const StateView &v, int b, int i) {
+  return v.dims[(int64_t)b * (v.n + 1) + i];
+}
+
+// ---------------------------------------------------------------- init
+template <typename R>
+__global__ void k_init_state(StateView v, double *discarded) {
+  const int b = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= v.n; i += gridDim.x * blockDim.x) {
+    v.dims[(int64_t)b * (v.n + 1) + i] = 1;
+    if (i < v.n) {
+      cx<R> *t = site_ptr<R>(v, b, i);
+      t[0] = mkc<R>(1, 0);  // |0>
+      t[1] = mkc<R>(0, 0);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) discarded[b] = 0.0;
+}
+
+// ---------------------------------------------------------------- K2
+// X = C_l (2Dl x Dm) * B_{l+1} (Dm x 2Dr) -> theta_buf (row-major, ld 2Dr)
+template <typename R>
+struct ProbTheta {
+  StateView v;
+  int l;
+  cx<R> *out;
+  int64_t tw;
+  const cx<R> *A, *B;
+  cx<R> *C;
+  int lda, ldb, ldc;
+  static constexpr bool A_KFAST = true, B_KFAST = false;
+  __device__ bool setup(int z, int &M, int &N, int &K) {
+    const int Dl = dimv(v, z, l), Dm = dimv(v, z, l + 1), Dr = dimv(v, z, l + 2);
+    M = 2 * Dl;
+    N = 2 * Dr;
+    K = Dm;
+    A = site_ptr<R>(v, z, l);
+    B = site_ptr<R>(v, z, l + 1);
+    C = out + (int64_t)z * tw;
+    lda = Dm;
+    ldb = 2 * Dr;
+    ldc = N;
+    return true;
+  }
+  __device__ cx<R> a(int i, int k) const { return A[(int64_t)i * lda + k]; }
+  __device__ cx<R> b(int k, int j) const { return B[(int64_t)k * ldb + j]; }
+  __device__ void store(int i, int j, cx<R> val) const { C[(int64_t)i * ldc + j] = val; }
+};
+
+// Theta = G X on the physical pair; writes theta_buf (in place) and the
+// column-major Jacobi copy in w_buf.
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_gate4(StateView v, Op2 op, const double *theta,
+                                                     int64_t ths, cx<R> *tbuf, cx<R> *wbuf,
+                                                     int64_t tw) {
+  const int b = blockIdx.y;
+  __shared__ cx<R> G[16];
+  if (threadIdx.x == 0) {
+    cx<double> Gd[16];
+    op2_matrix(op, theta ? theta + (int64_t)b * ths : nullptr, Gd);
+    for (int e = 0; e < 16; ++e) G[e] = mkc<R>((R)Gd[e].re, (R)Gd[e].im);
+  }
+  __syncthreads();
+  const int l = op.l;
+  const int Dl = dimv(v, b, l), Dr = dimv(v, b, l + 2);
+  const int M = 2 * Dl, N = 2 * Dr;
+  cx<R> *T = tbuf + (int64_t)b * tw;
+  cx<R> *W = wbuf + (int64_t)b * tw;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Dl * Dr; e += gridDim.x * blockDim.x) {
+    const int a = e / Dr, c = e - a * Dr;
+    cx<R> x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = T[(int64_t)(2 * a + (q >> 1)) * N + (q & 1) * Dr + c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cfma(acc, G[4 * r + q], x[q]);
+      const int i = 2 * a + (r >> 1), j = (r & 1) * Dr + c;
+      T[(int64_t)i * N + j] = acc;
+      W[(int64_t)j * M + i] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K4
+template <typename R>
+__global__ void __launch_bounds__(256) k_split_select(StateView v, int l, const cx<R> *wbuf,
+                                                      int64_t tw, double eps, double floor_eps,
+                                                      int cap, double *discarded, double *scale,
+                                                      uint32_t *err,
+                                                      unsigned long long *counters) {
+  const int b = blockIdx.x;
+  const int Dl = dimv(v, b, l), Dm = dimv(v, b, l + 1), Dr = dimv(v, b, l + 2);
+  const int M = 2 * Dl, N = 2 * Dr;
+  const cx<R> *W = wbuf + (int64_t)b * tw;
+  __shared__ double sig[TNMPS_JACOBI_MAX_DIM];
+  __shared__ int perm[TNMPS_JACOBI_MAX_DIM];
+  __shared__ int s_k;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < N; j += 8) {
+    double acc = 0;
+    for (int r = lane; r < M; r += 32) {
+      const cx<R> z = W[(int64_t)j * M + r];
+      acc += (double)z.re * z.re + (double)z.im * z.im;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sig[j] = sqrt(acc);
+  }
+  __syncthreads();
+  // stable descending rank
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double sj = sig[j];
+    int rank = 0;
+    for (int i = 0; i < N; ++i) {
+      const double si = sig[i];
+      rank += (si > sj) || (si == sj && i < j);
+    }
+    perm[rank] = j;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double total = 0;
+    for (int r = 0; r < N; ++r) total += sig[perm[r]] * sig[perm[r]];
+    const double norm = sqrt(total);
+    const double smax = sig[perm[0]];
+    (void)smax;
+    // the Jacobi noise floor (8u of the norm) is always cut: columns below it
+    // were not orthogonalised
+    const double e_eff = eps > floor_eps ? eps : floor_eps;
+    const double thr = e_eff * norm;
+    int keep = 0;
+    while (keep < N && sig[perm[keep]] >= thr && sig[perm[keep]] > 0) ++keep;
+    int kmax = cap < M ? cap : M;
+    kmax = kmax < N ? kmax : N;
+    int k = keep < kmax ? keep : kmax;
+    if (k < 1) k = 1;
+    double kept = 0;
+    for (int r = 0; r < k; ++r) kept += sig[perm[r]] * sig[perm[r]];
+    double w = 0;
+    for (int r = k; r < N; ++r) w += sig[perm[r]] * sig[perm[r]];
+    if (!(total > 0) || !isfinite(total)) {
+      atomicOr(err, TNMPS_EFLAG_NUMERIC);
+      kept = 1;
+      w = 0;
+      total = 1;
+    }
+    discarded[b] += w / total;
+    scale[b] = 1.0 / sqrt(kept);
+    v.dims[(int64_t)b * (v.n + 1) + l + 1] = k;
+    s_k = k;
+    atomicAdd(&counters[CNT_GATES2Q], 1ull);
+    if (Dl == v.chi && Dm == v.chi && Dr == v.chi) atomicAdd(&counters[CNT_GATES2Q_FULL], 1ull);
+  }
+  __syncthreads();
+  const int k = s_k;
+  cx<R> *A = site_ptr<R>(v, b, l);  // (Dl, 2, k) == M x k row-major
+  for (int e = threadIdx.x; e < M * k; e += blockDim.x) {
+    const int i = e / k, r = e - i * k;
+    const int j = perm[r];
+    const double s = sig[j];
+    const R inv = s > 0 ? (R)(1.0 / s) : R(0);
+    const cx<R> z = W[(int64_t)j * M + i];
+    A[e] = mkc<R>(z.re * inv, z.im * inv);
+  }
+}
+
+// C_{l+1} (k x 2Dr) = A_l^H (k x M) Theta (M x 2Dr); normalised afterwards
+template <typename R>
+struct ProbSplit {
+  StateView v;
+  int l;
+  const cx<R> *tb;
+  int64_t tw;
+  const cx<R> *A, *T;
+  cx<R> *C;
+  int k, N;
+  static constexpr bool A_KFAST = false, B_KFAST = false;
+  __device__ bool setup(int z, int &M_, int &N_, int &K_) {
+    const int Dl = dimv(v, z, l), Dr = dimv(v, z, l + 2);
+    k = dimv(v, z, l + 1);
+    N = 2 * Dr;
+    M_ = k;
+    N_ = N;
+    K_ = 2 * Dl;
+    A = site_ptr<R>(v, z, l);
+    T = tb + (int64_t)z * tw;
+    C = site_ptr<R>(v, z, l + 1);
+    return true;
+  }
+  __device__ cx<R> a(int r, int i) const { return cconj(A[(int64_t)i * k + r]); }
+  __device__ cx<R> b(int i, int j) const { return T[(int64_t)i * N + j]; }
+  __device__ void store(int r, int j, cx<R> val) const { C[(int64_t)r * N + j] = val; }
+};
+
+// complex64 form: E = U^H U - I with FP64 accumulation of the (exact) FP32
+// products -- the FP64 Gram of the orthogonalisation step
+struct ProbGram {
+  StateView v;
+  int l;
+  cx<double> *ebuf;
+  int64_t estride;
+  const cx<float> *U;
+  cx<double> *E;
+  int k;
+  static constexpr bool A_KFAST = false, B_KFAST = false;
+  __device__ bool setup(int z, int &M_, int &N_, int &K_) {
+    k = dimv(v, z, l + 1);
+    M_ = k;
+    N_ = k;
+    K_ = 2 * dimv(v, z, l);
+    U = site_ptr<float>(v, z, l);
+    E = ebuf + (int64_t)z * estride;
+    return true;
+  }
+  __device__ cx<double> a(int q, int i) const {
+    const cx<float> u = U[(int64_t)i * k + q];
+    return mkc<double>(u.re, -(double)u.im);
+  }
+  __device__ cx<double> b(int i, int q) const {
+    const cx<float> u = U[(int64_t)i * k + q];
+    return mkc<double>(u.re, u.im);
+  }
+  __device__ void store(int q, int r, cx<double> val) const {
+    E[(int64_t)q * k + r] = mkc<double>(val.re - (q == r ? 1.0 : 0.0), val.im);
+  }
+};
+
+// U' = U (I - E/2) -> w_buf (M x k row-major): first-order re-orthonormalisation
+struct ProbOrtho {
+  StateView v;
+  int l;
+  const cx<double> *ebuf;
+  int64_t estride;
+  cx<float> *wbuf;
+  int64_t tw;
+  const cx<float> *U;
+  const cx<double> *E;
+  cx<float> *O;
+  int k;
+  static constexpr bool A_KFAST = true, B_KFAST = false;
+  __device__ bool setup(int z, int &M_, int &N_, int &K_) {
+    k = dimv(v, z, l + 1);
+    M_ = 2 * dimv(v, z, l);
+    N_ = k;
+    K_ = k;
+    U = site_ptr<float>(v, z, l);
+    E = ebuf + (int64_t)z * estride;
+    O = wbuf + (int64_t)z * tw;
+    return true;
+  }
+  __device__ cx<float> a(int i, int q) const { return U[(int64_t)i * k + q]; }
+  __device__ cx<float> b(int q, int r) const {
+    const cx<double> e = E[(int64_t)q * k + r];
+    return mkc<float>((float)((q == r ? 1.0 : 0.0) - 0.5 * e.re), (float)(-0.5 * e.im));
+  }
+  __device__ void store(int i, int r, cx<float> val) const { O[(int64_t)i * k + r] = val; }
+};
+
+// A_l <- w_buf (M x k)
+__global__ void k_copy_u(StateView v, int l, const cx<float> *wbuf, int64_t tw) {
+  const int b = blockIdx.y;
+  const int cnt = 2 * dimv(v, b, l) * dimv(v, b, l + 1);
+  cx<float> *A = site_ptr<float>(v, b, l);
+  const cx<float> *W = wbuf + (int64_t)b * tw;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x)
+    A[e] = W[e];
+}
+
+// scale site tensor `site` of every state to unit Frobenius norm (FP64 sum):
+// the new orthogonality centre carries the whole (renormalised) state
+template <typename R>
+__global__ void __launch_bounds__(256) k_normalise_site(StateView v, int site) {
+  const int b = blockIdx.x;
+  const int cnt = dimv(v, b, site) * 2 * dimv(v, b, site + 1);
+  cx<R> *X = site_ptr<R>(v, b, site);
+  double acc = 0;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+    acc += (double)X[e].re * X[e].re + (double)X[e].im * X[e].im;
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double tot = 0;
+  for (int w = 0; w < 8; ++w) tot += red[w];
+  const R sc = tot > 0 ? (R)(1.0 / sqrt(tot)) : R(1);
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) X[e] = mkc<R>(X[e].re * sc, X[e].im * sc);
+}
+
+// ---------------------------------------------------------------- K1
+template <typename R>
+__global__ void __launch_bounds__(256) k_gate1(StateView v, Op1 op, const double *theta,
+                                               int64_t ths) {
+  const int b = blockIdx.y;
+  __shared__ cx<R> U[4];
+  if (threadIdx.x == 0) {
+    cx<double> Ud[4];
+    side_matrix(op.f, op.nf, theta ? theta + (int64_t)b * ths : nullptr, Ud);
+    for (int e = 0; e < 4; ++e) U[e] = mkc<R>((R)Ud[e].re, (R)Ud[e].im);
+  }
+  __syncthreads();
+  const int Dl = dimv(v, b, op.site), Dr = dimv(v, b, op.site + 1);
+  cx<R> *X = site_ptr<R>(v, b, op.site);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Dl * Dr; e += gridDim.x * blockDim.x) {
+    const int a = e / Dr, c = e - a * Dr;
+    const cx<R> x0 = X[(int64_t)(2 * a) * Dr + c], x1 = X[(int64_t)(2 * a + 1) * Dr + c];
+    cx<R> y0 = mkc<R>(0, 0), y1 = mkc<R>(0, 0);
+    cfma(y0, U[0], x0);
+    cfma(y0, U[1], x1);
+    cfma(y1, U[2], x0);
+    cfma(y1, U[3], x1);
+    X[(int64_t)(2 * a) * Dr + c] = y0;
+    X[(int64_t)(2 * a + 1) * Dr + c] = y1;
+  }
+}
+
+// ---------------------------------------------------------------- K7
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  R t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// In-place Householder QR of the column-major m x n matrix W (ld m):
+// afterwards R is the upper triangle and the reflector vectors (v_j with
+// implicit leading 1) sit below the diagonal; tau[j] holds their scalars
+// (H_j = I - tau_j v_j v_j^H, A = H_0 ... H_{r-1} R).
+template <typename R>
+__device__ void householder_qr(cx<R> *W, int m, int n, cx<R> *tau, R *red) {
+  const int r = m < n ? m : n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < r; ++j) {
+    cx<R> *col = W + (int64_t)j * m;
+    R part = 0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
+      part += col[i].re * col[i].re + col[i].im * col[i].im;
+    const R xn2 = block_sum(part, red);
+    const cx<R> alpha = col[j];
+    __syncthreads();
+    cx<R> tj = mkc<R>(0, 0);
+    if (!(xn2 == R(0) && alpha.im == R(0))) {
+      const R beta = -copysign(sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2), alpha.re);
+      tj = mkc<R>((beta - alpha.re) / beta, -alpha.im / beta);
+      // scal = 1 / (alpha - beta)
+      const R dr = alpha.re - beta, di = alpha.im;
+      const R den = dr * dr + di * di;
+      const cx<R> sc = mkc<R>(dr / den, -di / den);
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) col[i] = cmul(col[i], sc);
+      __syncthreads();
+      if (threadIdx.x == 0) col[j] = mkc<R>(beta, 0);
+    }
+    if (threadIdx.x == 0) tau[j] = tj;
+    __syncthreads();
+    if (tj.re == R(0) && tj.im == R(0)) continue;
+    // columns k > j:  x <- x - conj(tau) v (v^H x)
+    const cx<R> ct = cconj(tj);
+    for (int k = j + 1 + warp; k < n; k += nw) {
+      cx<R> *x = W + (int64_t)k * m;
+      cx<R> w = mkc<R>(0, 0);
+      for (int i = j + lane; i < m; i += 32) {
+        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : col[i];
+        cfma(w, cconj(vi), x[i]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+      }
+      const cx<R> f = cmul(ct, w);
+      for (int i = j + lane; i < m; i += 32) {
+        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : col[i];
+        const cx<R> d = cmul(f, vi);
+        x[i] = mkc<R>(x[i].re - d.re, x[i].im - d.im);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Q = H_0 ... H_{r-1} [I; 0] (m x r, column-major ld m) from the reflectors in W.
+template <typename R>
+__device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *tau, cx<R> *Q) {
+  const int r = m < n ? m : n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int q = e / m, i = e - q * m;
+    Q[e] = mkc<R>(i == q ? R(1) : R(0), 0);
+  }
+  __syncthreads();
+  for (int j = r - 1; j >= 0; --j) {
+    const cx<R> tj = tau[j];
+    if (tj.re == R(0) && tj.im == R(0)) continue;
+    const cx<R> *v = W + (int64_t)j * m;
+    for (int q = j + warp; q < r; q += nw) {
+      cx<R> *x = Q + (int64_t)q * m;
+      cx<R> w = mkc<R>(0, 0);
+      for (int i = j + lane; i < m; i += 32) {
+        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : v[i];
+        cfma(w, cconj(vi), x[i]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+      }
+      const cx<R> f = cmul(tj, w);
+      for (int i = j + lane; i < m; i += 32) {
+        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : v[i];
+        const cx<R> d = cmul(f, vi);
+        x[i] = mkc<R>(x[i].re - d.re, x[i].im - d.im);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Right move at site c: C_c (2Dl x Dr) = Q R;  A_c <- Q;  R stays in w_buf.
+template <typename R>
+__global__ void __launch_bounds__(256) k_qr_right(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
+                                                  int64_t tw, int32_t *newdim) {
+  const int b = blockIdx.x;
+  const int Dl = dimv(v, b, c), Dr = dimv(v, b, c + 1);
+  const int m = 2 * Dl, n = Dr, r = m < n ? m : n;
+  cx<R> *W = wbuf + (int64_t)b * tw, *Q = tbuf + (int64_t)b * tw;
+  cx<R> *X = site_ptr<R>(v, b, c);
+  __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
+  __shared__ R red[32];
+  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+    const int k = e / m, i = e - k * m;
+    W[e] = X[(int64_t)i * n + k];
+  }
+  __syncthreads();
+  householder_qr(W, m, n, tau, red);
+  householder_form_q(W, m, n, tau, Q);
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int i = e / r, q = e - i * r;
+    X[e] = Q[(int64_t)q * m + i];
+  }
+  if (threadIdx.x == 0) newdim[b] = r;
+}
+
+// Left move at site c: C_c (Dl x 2Dr) = L Q via QR of C_c^H = Q' R';
+// B_c <- Q'^H,  L = R'^H stays (as R') in w_buf.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lq_left(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
+                                                 int64_t tw, int32_t *newdim) {
+  const int b = blockIdx.x;
+  const int Dl = dimv(v, b, c), Dr = dimv(v, b, c + 1);
+  const int m = 2 * Dr, n = Dl, r = m < n ? m : n;
+  cx<R> *W = wbuf + (int64_t)b * tw, *Q = tbuf + (int64_t)b * tw;
+  cx<R> *X = site_ptr<R>(v, b, c);
+  __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
+  __shared__ R red[32];
+  for (int e = threadIdx.x; e < m * n; e += blockDim.x) W[e] = cconj(X[e]);  // column k = conj row k
+  __syncthreads();
+  householder_qr(W, m, n, tau, red);
+  householder_form_q(W, m, n, tau, Q);
+  for (int e = threadIdx.x; e < r * m; e += blockDim.x) X[e] = cconj(Q[e]);
+  if (threadIdx.x == 0) newdim[b] = r;
+}
+
+// out (r x 2D') = R (r x Dr, upper triangle of w_buf, ld 2Dl) * B_{c+1} (Dr x 2D')
+template <typename R>
+struct ProbRB {
+  StateView v;
+  int c;
+  const cx<R> *wbuf;
+  cx<R> *tbuf;
+  int64_t tw;
+  const int32_t *newdim;
+  const cx<R> *Wm, *B;
+  cx<R> *O;
+  int m, N;
+  static constexpr bool A_KFAST = false, B_KFAST = false;
+  __device__ bool setup(int z, int &M_, int &N_, int &K_) {
+    const int Dl = dimv(v, z, c), Dr = dimv(v, z, c + 1), D2 = dimv(v, z, c + 2);
+    m = 2 * Dl;
+    N = 2 * D2;
+    M_ = newdim[z];
+    N_ = N;
+    K_ = Dr;
+    Wm = wbuf + (int64_t)z * tw;
+    B = site_ptr<R>(v, z, c + 1);
+    O = tbuf + (int64_t)z * tw;
+    return true;
+  }
+  __device__ cx<R> a(int q, int k) const {
+    return k >= q ? Wm[(int64_t)k * m + q] : mkc<R>(0, 0);
+  }
+  __device__ cx<R> b(int k, int j) const { return B[(int64_t)k * N + j]; }
+  __device__ void store(int q, int j, cx<R> val) const { O[(int64_t)q * N + j] = val; }
+};
+
+// out (2D'' x r) = A_{c-1} (2D'' x Dl) * L (Dl x r), L[k][q] = conj(R'[q][k])
+template <typename R>
+struct ProbAL {
+  StateView v;
+  int c;
+  const cx<R> *wbuf;
+  cx<R> *tbuf;
+  int64_t tw;
+  const int32_t *newdim;
+  const cx<R> *Wm, *A;
+  cx<R> *O;
+  int m, Dl, r;
+  static constexpr bool A_KFAST = true, B_KFAST = false;
+  __device__ bool setup(int z, int &M_, int &N_, int &K_) {
+    const int D0 = dimv(v, z, c - 1);
+    Dl = dimv(v, z, c);
+    m = 2 * dimv(v, z, c + 1);
+    r = newdim[z];
+    M_ = 2 * D0;
+    N_ = r;
+    K_ = Dl;
+    Wm = wbuf + (int64_t)z * tw;
+    A = site_ptr<R>(v, z, c - 1);
+    O = tbuf + (int64_t)z * tw;
+    return true;
+  }
+  __device__ cx<R> a(int i, int k) const { return A[(int64_t)i * Dl + k]; }
+  __device__ cx<R> b(int k, int q) const {
+    return k >= q ? cconj(Wm[(int64_t)k * m + q]) : mkc<R>(0, 0);
+  }
+  __device__ void store(int i, int q, cx<R> val) const { O[(int64_t)i * r + q] = val; }
+};
+
+// site `dst` <- tbuf (elements = rows * cols), then dims[b][bond] = newdim[b]
+template <typename R>
+__global__ void k_copy_site(StateView v, int dst, int bond, int rows_idx, int cols_idx,
+                            bool rows_from_new, const cx<R> *tbuf, int64_t tw,
+                            const int32_t *newdim) {
+  const int b = blockIdx.y;
+  const int nd = newdim[b];
+  const int rows = rows_from_new ? nd : 2 * dimv(v, b, rows_idx);
+  const int cols = rows_from_new ? 2 * dimv(v, b, cols_idx) : nd;
+  const int64_t cnt = (int64_t)rows * cols;
+  cx<R> *X = site_ptr<R>(v, b, dst);
+  const cx<R> *T = tbuf + (int64_t)b * tw;
+  for (int64_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x)
+    X[e] = T[e];
+}
+
+__global__ void k_set_bond(StateView v, int bond, const int32_t *newdim) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < v.batch) v.dims[(int64_t)b * (v.n + 1) + bond] = newdim[b];
+}
+
+template <typename R>
+cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t ths) {
+  const StateView v = c->view();
+  const int l = op.l;
+  const int Mmax = 2 * c->ub[l], Nmax = 2 * c->ub[l + 2];
+  cx<R> *tb = reinterpret_cast<cx<R> *>(c->theta_buf);
+  cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
+  cudaError_t e;
+  // K2: Theta = G (C_l B_{l+1})
+  cudaEvent_t ev = prof_begin(c, PC_THETA);
+  ProbTheta<R> pt{};
+  pt.v = v;
+  pt.l = l;
+  pt.out = tb;
+  pt.tw = c->tw;
+  if ((e = launch_gemm<R>(pt, Mmax, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
+    return e;
+  {
+    const int work = c->ub[l] * c->ub[l + 2];
+    dim3 grid((work + 255) / 256, c->batch);
+    k_apply_gate4<R><<<grid, 256, 0, c->stream>>>(v, op, theta, ths, tb, wb, c->tw);
+    ++c->launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  prof_end(c, PC_THETA, ev);
+  // K3: one-sided Jacobi on the column-major copy
+  ev = prof_begin(c, PC_JACOBI);
+  if ((e = launch_jacobi_gate(c, l, Mmax)) != cudaSuccess) return e;
+  ++c->launches;
+  prof_end(c, PC_JACOBI, ev);
+  // K4: rank, A_l <- U_k, [orthonormalise U_k], C_{l+1} <- U_k^H Theta, normalise
+  ev = prof_begin(c, PC_SPLIT);
+  const double floor_eps =
+      c->dtype == TNMPS_C64 ? 8.0 * 5.9604644775390625e-08 : 8.0 * 1.1102230246251565e-16;
+  k_split_select<R><<<c->batch, 256, 0, c->stream>>>(v, l, wb, c->tw, c->eps, floor_eps,
+                                                      c->cap[l + 1], c->discarded, c->scale,
+                                                      c->err, c->counters);
+  ++c->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int kub = c->cap[l + 1];
+  kub = kub < Mmax ? kub : Mmax;
+  kub = kub < Nmax ? kub : Nmax;
+  if (sizeof(R) == 4) {
+    ProbGram pg{};
+    pg.v = v;
+    pg.l = l;
+    pg.ebuf = reinterpret_cast<cx<double> *>(c->ebuf);
+    pg.estride = (int64_t)c->chi * c->chi;
+    if ((e = launch_gemm<double>(pg, kub, kub, c->batch, c->stream, &c->launches)) != cudaSuccess)
+      return e;
+    ProbOrtho po{};
+    po.v = v;
+    po.l = l;
+    po.ebuf = pg.ebuf;
+    po.estride = pg.estride;
+    po.wbuf = reinterpret_cast<cx<float> *>(c->w_buf);
+    po.tw = c->tw;
+    if ((e = launch_gemm<float>(po, Mmax, kub, c->batch, c->stream, &c->launches)) != cudaSuccess)
+      return e;
+    dim3 grid((Mmax * kub + 255) / 256, c->batch);
+    k_copy_u<<<grid, 256, 0, c->stream>>>(v, l, reinterpret_cast<cx<float> *>(c->w_buf), c->tw);
+    ++c->launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  ProbSplit<R> ps{};
+  ps.v = v;
+  ps.l = l;
+  ps.tb = tb;
+  ps.tw = c->tw;
+  if ((e = launch_gemm<R>(ps, kub, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
+    return e;
+  k_normalise_site<R><<<c->batch, 256, 0, c->stream>>>(v, l + 1);
+  ++c->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  prof_end(c, PC_SPLIT, ev);
+  c->ub[l + 1] = kub;
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t move_right_impl(tnmps_ctx *c, int s) {
+  const StateView v = c->view();
+  cx<R> *tb = reinterpret_cast<cx<R> *>(c->theta_buf);
+  cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
+  cudaEvent_t ev = prof_begin(c, PC_MOVE);
+  k_qr_right<R><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
+  c->launches += 4;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int rub = 2 * c->ub[s];
+  rub = rub < c->ub[s + 1] ? rub : c->ub[s + 1];
+  ProbRB<R> p{};
+  p.v = v;
+  p.c = s;
+  p.wbuf = wb;
+  p.tbuf = tb;
+  p.tw = c->tw;
+  p.newdim = c->perm;
+  if ((e = launch_gemm<R>(p, rub, 2 * c->ub[s + 2], c->batch, c->stream)) != cudaSuccess) return e;
+  const int64_t cnt = (int64_t)rub * 2 * c->ub[s + 2];
+  dim3 grid((unsigned)((cnt + 255) / 256), c->batch);
+  k_copy_site<R><<<grid, 256, 0, c->stream>>>(v, s + 1, s + 1, 0, s + 2, true, tb, c->tw, c->perm);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_set_bond<<<(c->batch + 255) / 256, 256, 0, c->stream>>>(v, s + 1, c->perm);
+  prof_end(c, PC_MOVE, ev);
+  c->ub[s + 1] = rub;
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t move_left_impl(tnmps_ctx *c, int s) {
+  const StateView v = c->view();
+  cx<R> *tb = reinterpret_cast<cx<R> *>(c->theta_buf);
+  cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
+  cudaEvent_t ev = prof_begin(c, PC_MOVE);
+  k_lq_left<R><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
+  c->launches += 4;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int rub = 2 * c->ub[s + 1];
+  rub = rub < c->ub[s] ? rub : c->ub[s];
+  ProbAL<R> p{};
+  p.v = v;
+  p.c = s;
+  p.wbuf = wb;
+  p.tbuf = tb;
+  p.tw = c->tw;
+  p.newdim = c->perm;
+  if ((e = launch_gemm<R>(p, 2 * c->ub[s - 1], rub, c->batch, c->stream)) != cudaSuccess) return e;
+  const int64_t cnt = (int64_t)2 * c->ub[s - 1] * rub;
+  dim3 grid((unsigned)((cnt + 255) / 256), c->batch);
+  k_copy_site<R><<<grid, 256, 0, c->stream>>>(v, s - 1, s, s - 1, 0, false, tb, c->tw, c->perm);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_set_bond<<<(c->batch + 255) / 256, 256, 0, c->stream>>>(v, s, c->perm);
+  prof_end(c, PC_MOVE, ev);
+  c->ub[s] = rub;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init_state(tnmps_ctx *c) {
+  dim3 grid((c->n + 1 + 255) / 256, c->batch);
+  ++c->launches;
+  if (c->dtype == TNMPS_C128)
+    k_init_state<double><<<grid, 256, 0, c->stream>>>(c->view(), c->discarded);
+  else
+    k_init_state<float><<<grid, 256, 0, c->stream>>>(c->view(), c->discarded);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate2(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t ths) {
+  return c->dtype == TNMPS_C128 ? gate2_impl<double>(c, op, theta, ths)
+                                : gate2_impl<float>(c, op, theta, ths);
+}
+
+cudaError_t launch_gate1(tnmps_ctx *c, const Op1 &op, const double *theta, int64_t ths) {
+  const int work = c->ub[op.site] * c->ub[op.site + 1];
+  dim3 grid((work + 255) / 256, c->batch);
+  ++c->launches;
+  if (c->dtype == TNMPS_C128)
+    k_gate1<double><<<grid, 256, 0, c->stream>>>(c->view(), op, theta, ths);
+  else
+    k_gate1<float><<<grid, 256, 0, c->stream>>>(c->view(), op, theta, ths);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move_right(tnmps_ctx *c, int s) {
+  return c->dtype == TNMPS_C128 ? move_right_impl<double>(c, s) : move_right_impl<float>(c, s);
+}
+
+cudaError_t launch_move_left(tnmps_ctx *c, int s) {
+  return c->dtype == TNMPS_C128 ? move_left_impl<double>(c, s) : move_left_impl<float>(c, s);
+}

@@ -1,0 +1,232 @@
+// Internal declarations shared by the CUDA translation units of libtnmps.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tnmps.h"
+
+// ---------------------------------------------------------------- complex
+template <typename R>
+struct alignas(2 * sizeof(R)) cx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mkc(R a, R b) {
+  cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
+  return mkc<R>(a.re + b.re, a.im + b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return mkc<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cconj(cx<R> a) {
+  return mkc<R>(a.re, -a.im);
+}
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cx<R> &acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+
+// ---------------------------------------------------------------- limits
+#define TNMPS_MAX_CHI 256
+#define TNMPS_MAX_FAC 8          // fused single-qubit factors per side of one op
+#define TNMPS_JACOBI_MAX_DIM 512
+
+// device error flag bits
+#define TNMPS_EFLAG_NOT_CONVERGED 1u
+#define TNMPS_EFLAG_NUMERIC 2u
+
+// device counter slots (uint64)
+enum {
+  CNT_GATES2Q = 0,
+  CNT_GATES2Q_FULL,
+  CNT_PAIR_ROWS,
+  CNT_ROTATIONS,
+  CNT_SWEEPS,
+  CNT_SVDS,
+  CNT_ENV_UPDATES,
+  CNT_ENV_FLOPS,
+  CNT_ROT_ROWS,
+  CNT_NUM
+};
+
+// kernel classes for event timing (mirrors tnmps_prof_class in tnmps.h)
+enum { PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_NUM };
+
+// ---------------------------------------------------------------- ops
+// A single-qubit factor: fixed 2x2 (kind 0, row-major complex in m[]) or a
+// parameterised rotation (kind 1/2/3 = RX/RY/RZ) of angle
+// angle + scale * theta[param] (param < 0: angle alone).
+struct Fac1 {
+  int32_t kind, param;
+  double angle, scale;
+  double m[8];
+};
+
+// Fused two-qubit op on sites (l, l+1): G = core * (U_l (x) U_{l+1}), where
+// U_s = f_{k-1} ... f_1 f_0 of the side's factor list; core is a fixed 4x4
+// (row-major complex, basis 2*s_l + s_{l+1}).
+struct Op2 {
+  int32_t l, nl, nr, pad;
+  double core[32];
+  Fac1 fl[TNMPS_MAX_FAC];
+  Fac1 fr[TNMPS_MAX_FAC];
+};
+
+// Standalone single-qubit op on one site.
+struct Op1 {
+  int32_t site, nf, pad0, pad1;
+  Fac1 f[TNMPS_MAX_FAC];
+};
+
+// ---------------------------------------------------------------- layout
+// Device view of the batched MPS, passed by value to kernels.
+struct StateView {
+  void *sites;            // complex elements, state b at sites + b*state_elems
+  const int64_t *site_off;  // device: element offset of each site in a state
+  int32_t *dims;          // [batch][n+1]: dims[b][i] = D_{i-1}; D_{-1} = D_{n-1} = 1
+  int64_t state_elems;
+  int32_t n, batch, chi;
+};
+
+struct tnmps_ctx {
+  int n = 0, chi = 0, batch = 0, max_params = 0;
+  tnmps_dtype dtype = TNMPS_C128;
+  double eps = 1e-4;
+  cudaStream_t stream = nullptr;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+
+  // carved device regions
+  void *sites = nullptr;
+  int64_t *site_off_dev = nullptr;
+  int32_t *dims = nullptr;
+  void *theta_buf = nullptr;   // [batch][tw] row-major Theta (gate applied)
+  void *w_buf = nullptr;       // [batch][tw] column-major Jacobi working copy
+  double *sigma = nullptr;     // [batch][2chi]
+  int32_t *perm = nullptr;     // [batch][2chi]
+  double *scale = nullptr;     // [batch]
+  double *discarded = nullptr; // [batch]
+  double *theta_dev = nullptr; // [batch][max_params]
+  uint32_t *err = nullptr;     // device flags
+  unsigned long long *counters = nullptr;  // [CNT_NUM]
+  void *ebuf = nullptr;        // [batch][chi^2] complex128 Gram (complex64 form)
+
+  // instrumentation: host-side launch count and optional per-class event timing
+  uint64_t launches = 0;
+  uint32_t prof_mask = 0;
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_open;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[PC_NUM] = {0};
+  uint64_t prof_cnt[PC_NUM] = {0};
+
+  std::vector<int64_t> site_off;  // host copy
+  std::vector<int> cap;           // bond capacity, size n+1 (cap[0] = cap[n] = 1)
+  int64_t state_elems = 0;
+  int64_t tw = 0;                 // (2 chi)^2
+
+  // host-side planning state; centre -1 = product state (any site may be the centre)
+  int centre = -1;
+  std::vector<int> ub;            // upper bound of dims per bond index 0..n
+  std::string last_error;
+  int inject_nth = 0;
+  tnmps_status inject_status = TNMPS_OK;
+  int call_count = 0;
+
+  // last uploaded term plan (skip re-upload)
+  const void *plan_terms = nullptr;
+  void *plan_ws = nullptr;
+  uint64_t plan_gen = 0;
+
+  StateView view() const {
+    StateView v;
+    v.sites = sites;
+    v.site_off = site_off_dev;
+    v.dims = dims;
+    v.state_elems = state_elems;
+    v.n = n;
+    v.batch = batch;
+    v.chi = chi;
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------- timing
+inline cudaEvent_t prof_event(tnmps_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+inline cudaEvent_t prof_begin(tnmps_ctx *c, int cls) {
+  if (!(c->prof_mask & (1u << cls))) return nullptr;
+  cudaEvent_t a = prof_event(c);
+  cudaEventRecord(a, c->stream);
+  return a;
+}
+inline void prof_end(tnmps_ctx *c, int cls, cudaEvent_t a) {
+  if (!a) return;
+  cudaEvent_t b = prof_event(c);
+  cudaEventRecord(b, c->stream);
+  c->prof_open.push_back({cls, a, b});
+}
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaSuccess or the launch error. dtype dispatch inside.
+cudaError_t launch_init_state(tnmps_ctx *c);
+cudaError_t launch_gate2(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t th_stride);
+cudaError_t launch_gate1(tnmps_ctx *c, const Op1 &op, const double *theta, int64_t th_stride);
+cudaError_t launch_move_right(tnmps_ctx *c, int site);
+cudaError_t launch_move_left(tnmps_ctx *c, int site);
+cudaError_t launch_jacobi_standalone(tnmps_dtype dt, int batch, int m, int n, void *a, int lda,
+                                     double *sigma, int32_t *sweeps, int max_sweeps,
+                                     cudaStream_t s);
+
+// expectation plan (built on the host)
+struct TermPlan {
+  int n = 0;
+  int64_t n_terms = 0;
+  int32_t depth = 0;
+  // trie nodes grouped by level; node ids are level-local
+  std::vector<int64_t> level_start;   // size depth+1: offsets into node arrays
+  std::vector<int32_t> node_site;     // site of each node
+  std::vector<int32_t> node_parent;   // parent index within previous level, -1 = identity start
+  std::vector<uint8_t> node_pauli;    // Pauli applied at node_site (0..3)
+  // terms attached per level: (term index, node index within level)
+  std::vector<int64_t> tlevel_start;  // size depth+1
+  std::vector<int32_t> tterm;
+  std::vector<int32_t> tnode;
+  std::vector<int32_t> tsite;         // end site b of the term
+  std::vector<int32_t> identity_terms;
+  std::vector<double> coeffs;
+  int64_t max_level_nodes = 0;
+  int64_t max_level_terms = 0;
+};
+
+cudaError_t expect_run(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_bytes, int chunk,
+                       double *energy_dev, double *per_term_dev, double **energy_used,
+                       double **per_term_used);
+size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk);

@@ -1,0 +1,313 @@
+"""Thin ctypes binding of ``libtnmps.so`` (the C ABI in ``include/tnmps.h``).
+
+Argument marshalling only: every step of circuit application and energy
+evaluation runs in the library's CUDA kernels. PyTorch provides device
+memory (the context arena and expectation workspaces are uint8 CUDA tensors)
+and the current CUDA stream. There is no CPU fallback: importing this module
+without the built library, or using it without a CUDA device, raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libtnmps.so")
+
+OPS = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "RX": 8, "RY": 9,
+       "RZ": 10, "CNOT": 16, "CZ": 17, "SWAP": 18}
+DTYPES = {"c128": 0, "c64": 1}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOMEM", 3: "ERR_UNSUPPORTED", 4: "ERR_NOT_CONVERGED",
+          5: "ERR_NUMERIC", 6: "ERR_CUDA", 7: "ERR_INJECTED"}
+
+
+class TnmpsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Gate(C.Structure):
+    _fields_ = [("op", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32), ("param", C.c_int32),
+                ("angle", C.c_double), ("scale", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("gates2q", "gates2q_full", "jacobi_pair_rows",
+                                          "jacobi_rotations", "jacobi_sweeps", "svds",
+                                          "env_updates", "env_flops", "jacobi_rot_rows",
+                                          "launches")]
+
+
+PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term")
+
+
+_lib = None
+
+
+def lib():
+    """Load the library once; raise if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libtnmps.so not built ({_LIB_PATH}); run "
+                           "`python -m paper_1807_07914_gb300.build`")
+    L = C.CDLL(_LIB_PATH)
+    P, I, S, D = C.c_void_p, C.c_int, C.c_size_t, C.c_double
+    sig = {
+        "tnmps_status_string": (C.c_char_p, [I]),
+        "tnmps_version": (C.c_char_p, []),
+        "tnmps_state_bytes": (S, [I, I, I, I, I]),
+        "tnmps_init": (I, [C.POINTER(P), I, I, I, I, I, P, S]),
+        "tnmps_free": (None, [P]),
+        "tnmps_set_cutoff": (I, [P, D]),
+        "tnmps_set_stream": (I, [P, P]),
+        "tnmps_reset": (I, [P]),
+        "tnmps_apply_circuit": (I, [P, P, S, P, S]),
+        "tnmps_apply_circuit_batched": (I, [P, P, S, P, S]),
+        "tnmps_apply_circuit_batched_dev": (I, [P, P, S, P, S]),
+        "tnmps_terms_create": (I, [C.POINTER(P), I, P, P, P, P, S]),
+        "tnmps_terms_free": (None, [P]),
+        "tnmps_terms_info": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int64)]),
+        "tnmps_expect_workspace_bytes": (S, [P, P, I]),
+        "tnmps_expect_pauli_sum": (I, [P, P, P, S, P, P]),
+        "tnmps_expect_pauli_sum_dev": (I, [P, P, P, S, P, P]),
+        "tnmps_check": (I, [P]),
+        "tnmps_get_bond_dims": (I, [P, P]),
+        "tnmps_get_discarded_weight": (I, [P, P]),
+        "tnmps_get_site": (I, [P, I, I, P, S, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "tnmps_get_centre": (I, [P]),
+        "tnmps_get_stats": (I, [P, C.POINTER(Stats)]),
+        "tnmps_last_error": (C.c_char_p, [P]),
+        "tnmps_jacobi_svd_dev": (I, [I, I, I, I, P, I, P, P, I, P]),
+        "tnmps_debug_inject": (I, [P, I, I]),
+        "tnmps_profile": (I, [P, C.c_uint32]),
+        "tnmps_profile_read": (I, [P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def gate_array(circuit):
+    """Gate records (name, q0, q1, param, angle, scale) -> ctypes array."""
+    arr = (Gate * max(len(circuit), 1))()
+    for i, (name, q0, q1, param, angle, scale) in enumerate(circuit):
+        arr[i] = Gate(OPS[name], int(q0), int(q1 if q1 is not None else -1),
+                      int(param if param is not None else -1), float(angle), float(scale))
+    return arr
+
+
+def _stream_handle(device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class PauliSum:
+    """A term set in the library's trie form (host side)."""
+
+    def __init__(self, n_qubits, terms):
+        off, sites, paulis, coeffs = _csr(terms)
+        self.n = int(n_qubits)
+        self.n_terms = len(terms)
+        h = C.c_void_p()
+        st = lib().tnmps_terms_create(C.byref(h), self.n, _ptr(off), _ptr(sites), _ptr(paulis),
+                                      _ptr(coeffs), self.n_terms)
+        if st != 0:
+            raise TnmpsError(st, "invalid Pauli terms")
+        self._h = h
+        self._keep = (off, sites, paulis, coeffs)
+
+    def info(self):
+        nn, dep, ml = C.c_int64(), C.c_int32(), C.c_int64()
+        lib().tnmps_terms_info(self._h, C.byref(nn), C.byref(dep), C.byref(ml))
+        return {"nodes": nn.value, "depth": dep.value, "max_level_nodes": ml.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tnmps_terms_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def _csr(terms):
+    off = [0]
+    s, p, c = [], [], []
+    for coeff, sites, paulis in terms:
+        s += [int(x) for x in sites]
+        p += [int(x) for x in paulis]
+        off.append(len(s))
+        c.append(float(coeff))
+    return (np.asarray(off, np.int32), np.asarray(s if s else [0], np.int32),
+            np.asarray(p if p else [0], np.uint8), np.asarray(c if c else [0.0], np.float64))
+
+
+class MPSBatch:
+    """``batch`` MPS states of ``n`` qubits on one CUDA device."""
+
+    def __init__(self, n, chi_max, batch=1, dtype="c128", max_params=0, eps=1e-4,
+                 device="cuda:0"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("tnmps needs a CUDA device; there is no CPU fallback")
+        L = lib()
+        self.device = torch.device(device)
+        self.n, self.chi, self.batch, self.dtype = int(n), int(chi_max), int(batch), dtype
+        self.max_params = int(max_params)
+        nbytes = L.tnmps_state_bytes(self.n, self.chi, DTYPES[dtype], self.batch, self.max_params)
+        if nbytes == 0:
+            raise TnmpsError(1, "invalid sizes")
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            h = C.c_void_p()
+            st = L.tnmps_init(C.byref(h), self.n, self.chi, DTYPES[dtype], self.batch,
+                              self.max_params, _ptr(self.arena), nbytes)
+        if st != 0:
+            raise TnmpsError(st, "init failed")
+        self._h = h
+        self._ws = {}
+        self.set_stream()
+        self.set_cutoff(eps)
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st):
+        if st != 0:
+            raise TnmpsError(st, lib().tnmps_last_error(self._h).decode())
+
+    def set_stream(self, stream=None):
+        s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(
+            self.device).cuda_stream
+        self._check(lib().tnmps_set_stream(self._h, C.c_void_p(s)))
+
+    def set_cutoff(self, eps):
+        self._check(lib().tnmps_set_cutoff(self._h, float(eps)))
+
+    def reset(self):
+        self._check(lib().tnmps_reset(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tnmps_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+    # -------------------------------------------------------------- circuits
+    def apply_circuit(self, circuit, thetas=None):
+        """thetas: None, [n_params] (shared) or [batch, n_params] (host)."""
+        g = gate_array(circuit)
+        if thetas is None:
+            self._check(lib().tnmps_apply_circuit(self._h, g, len(circuit), None, 0))
+            return
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64))
+        if th.ndim == 1:
+            self._check(lib().tnmps_apply_circuit(self._h, g, len(circuit), _ptr(th), th.size))
+        else:
+            assert th.shape[0] == self.batch
+            self._check(lib().tnmps_apply_circuit_batched(self._h, g, len(circuit), _ptr(th),
+                                                          th.shape[1]))
+
+    def apply_circuit_dev(self, gates_c, thetas_dev, n_gates=None):
+        """Asynchronous: gates_c from gate_array(), thetas_dev a float64 CUDA
+        tensor [batch, n_params]."""
+        assert thetas_dev.is_cuda and thetas_dev.dtype == torch.float64
+        ng = len(gates_c) if n_gates is None else n_gates
+        self._check(lib().tnmps_apply_circuit_batched_dev(self._h, gates_c, ng, _ptr(thetas_dev),
+                                                          thetas_dev.shape[-1]))
+
+    # -------------------------------------------------------------- energies
+    def workspace(self, terms, chunk=0):
+        key = (id(terms), chunk)
+        ws = self._ws.get(key)
+        if ws is None:
+            nb = lib().tnmps_expect_workspace_bytes(self._h, terms._h, int(chunk))
+            if nb == 0:
+                raise TnmpsError(1, "workspace size query failed")
+            ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+            self._ws = {key: ws}
+        return ws
+
+    def expect(self, terms, per_term=False, chunk=0):
+        """Energies [batch] (and Re<P_k> [batch, T]) as numpy, synchronous."""
+        ws = self.workspace(terms, chunk)
+        e = np.zeros(self.batch, np.float64)
+        pt = np.zeros((self.batch, terms.n_terms), np.float64) if per_term else None
+        self._check(lib().tnmps_expect_pauli_sum(self._h, terms._h, _ptr(ws), ws.numel(),
+                                                 _ptr(e), _ptr(pt)))
+        return (e, pt) if per_term else e
+
+    def expect_dev(self, terms, energy, per_term=None, chunk=0):
+        """Asynchronous: energy (and per_term) float64 CUDA tensors."""
+        ws = self.workspace(terms, chunk)
+        self._check(lib().tnmps_expect_pauli_sum_dev(self._h, terms._h, _ptr(ws), ws.numel(),
+                                                     _ptr(energy), _ptr(per_term)))
+
+    # -------------------------------------------------------------- inspection
+    def check(self):
+        self._check(lib().tnmps_check(self._h))
+
+    def bond_dims(self):
+        d = np.zeros((self.batch, max(self.n - 1, 1)), np.int32)
+        self._check(lib().tnmps_get_bond_dims(self._h, _ptr(d)))
+        return d[:, : self.n - 1]
+
+    def discarded(self):
+        w = np.zeros(self.batch, np.float64)
+        self._check(lib().tnmps_get_discarded_weight(self._h, _ptr(w)))
+        return w
+
+    def site(self, b, i):
+        cap = self.chi * 2 * self.chi
+        buf = np.zeros(2 * cap, np.float64)
+        dl, dr = C.c_int32(), C.c_int32()
+        self._check(lib().tnmps_get_site(self._h, b, i, _ptr(buf), cap, C.byref(dl), C.byref(dr)))
+        z = buf[: 2 * dl.value * 2 * dr.value].view(np.complex128)
+        return z.reshape(dl.value, 2, dr.value)
+
+    def centre(self):
+        return lib().tnmps_get_centre(self._h)
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().tnmps_get_stats(self._h, C.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+    def profile(self, classes=PROF_CLASSES):
+        """Start CUDA-event timing of the named kernel classes (None = stop)."""
+        mask = 0
+        for k in classes or ():
+            mask |= 1 << PROF_CLASSES.index(k)
+        self._check(lib().tnmps_profile(self._h, mask))
+
+    def profile_read(self):
+        ms = np.zeros(len(PROF_CLASSES), np.float64)
+        cnt = np.zeros(len(PROF_CLASSES), np.uint64)
+        self._check(lib().tnmps_profile_read(self._h, _ptr(ms), _ptr(cnt)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def inject(self, nth, status):
+        self._check(lib().tnmps_debug_inject(self._h, int(nth), int(status)))
+
+
+def jacobi_svd_dev(a, m, n, sigma, sweeps, max_sweeps=0, stream=None):
+    """One-sided Jacobi on a [batch, n, lda] complex CUDA tensor (column j of
+    matrix b is a[b, j, :m]); in place. sigma float64 [batch, n], sweeps int32
+    [batch]."""
+    dt = {torch.complex128: 0, torch.complex64: 1}[a.dtype]
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(a.device).cuda_stream
+    st = lib().tnmps_jacobi_svd_dev(dt, a.shape[0], int(m), int(n), _ptr(a), a.shape[2],
+                                    _ptr(sigma), _ptr(sweeps), int(max_sweeps), C.c_void_p(s))
+    if st != 0:
+        raise TnmpsError(st, "jacobi_svd_dev failed")
