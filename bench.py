@@ -1,0 +1,375 @@
+"""Throughput benchmark: MPS simulation of a parameterised ansatz plus its
+Pauli-sum energy, at chi=128 on 40 qubits.
+
+One step = the whole hot path for one batch of parameter vectors:
+reset to |0...0>, apply the 10-layer Ry/Rz + CNOT-ladder ansatz (390
+two-qubit gates per state, the middle bonds saturate at chi=128 after 7
+layers), then evaluate E(theta) = sum_k c_k <P_k> over the 157-term
+Heisenberg chain for every state.
+
+Prints ONE JSON line. ``value`` = Pauli-term expectations per second
+(whole job: states x terms / step time, the state simulation included);
+``gates_per_s`` = two-qubit gate applications per second; the dominant
+kernel's roofline (the one-sided Jacobi SVD) is measured live with CUDA
+events on the library's stream.
+
+  python bench.py [--gpus N --steps K --warmup W] [--dtype c64|c128] [--batch B]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+Under torchrun each rank simulates its own batch (replicas; weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1807_07914_gb300 import inputs  # noqa: E402
+
+METRIC = "Pauli-term expectations/sec and gates/sec at chi=128, 40 qubits; % roofline"
+UNIT = "expectations/s"
+FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
+N_SMS = 152
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (nominal)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def workload_cfg(args):
+    wl = inputs.workload("chi128", rep=args.rank_seed)
+    n, chi, eps = wl["n"], wl["chi_max"], wl["eps"]
+    return wl, n, chi, eps
+
+
+def config_dict(args, n, chi, B, P, T, state_bytes):
+    return {
+        "workload": f"hea40_chi128: n={n}, 10 layers (Ry,Rz on every qubit; CNOT ladder), "
+                    f"chi_max={chi}, cutoff 1e-10, {B} theta/GPU, Heisenberg chain {T} terms",
+        "n_qubits": n, "chi_max": chi, "layers": 10, "params": P, "batch_per_gpu": B,
+        "terms": T, "gates2q_per_state": 390,
+        "l2": f"inputs larger than L2 (state arena {state_bytes / 2**30:.2f} GiB per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x, ws, device=None):
+    """Max of a float over ranks (timing only; not on the data path)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(wl, n_theta=1, n_terms=None):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the same
+    workload: the full circuit for n_theta parameter rows and the per-term
+    energy sweeps. Returns (seconds, states, terms_per_state, gates)."""
+    from oracle import mps as OM
+    terms = wl["terms"] if n_terms is None else wl["terms"][:n_terms]
+    t0 = time.perf_counter()
+    gates = 0
+    for b in range(n_theta):
+        m = OM.MPS(wl["n"], wl["chi_max"], wl["eps"]).run(wl["circuit"], wl["thetas"][b])
+        gates += len(m.step_weights)
+        e = 0.0
+        for c, s, p in terms:
+            e += c * m.expect_pauli(s, p).real
+    return time.perf_counter() - t0, n_theta, len(terms), gates
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(wl):
+    dt, states, T, gates = oracle_sample(wl, 1)
+    return {"value": states * T / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "gates_per_s": gates / dt,
+            "sample": f"FP64 oracle (numpy/LAPACK) on 1 of the theta rows: full 390-gate "
+                      f"circuit + {T} per-term sweeps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    wl, n, chi, eps = workload_cfg(args)
+    for _ in range(args.warmup):
+        oracle_sample(wl, 1)
+    times = []
+    tot_terms = 0
+    for _ in range(args.steps):
+        dt, states, T, gates = oracle_sample(wl, 1)
+        times.append(dt)
+        tot_terms += states * T
+    tot = sum(times)
+    v = tot_terms / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": config_dict(args, n, chi, 1, wl["n_params"], len(wl["terms"]), 0),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                         "sample": "per step: 1 theta row, full circuit + all terms"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    from paper_1807_07914_gb300 import tnmps
+
+    args.rank_seed = rank
+    wl, n, chi, eps = workload_cfg(args)
+    B = args.batch
+    P = wl["n_params"]
+    th = inputs.thetas(B, P, inputs.rng_for(5, 100 + rank))
+    if rank == 0:
+        th[0] = wl["thetas"][0]        # the row the CPU baseline samples
+    terms = wl["terms"]
+    T = len(terms)
+    m = tnmps.MPSBatch(n, chi, B, dtype=args.dtype, max_params=P, eps=eps, device=device)
+    ps = tnmps.PauliSum(n, terms)
+    gates_c = tnmps.gate_array(wl["circuit"])
+    th_dev = torch.tensor(th, dtype=torch.float64, device=device)
+    energy = torch.empty(B, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step(ev=None):
+        m.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        m.apply_circuit_dev(gates_c, th_dev)
+        if ev is not None:
+            ev[1].record(stream)
+        m.expect_dev(ps, energy)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    m.check()
+    # ---- timed region (device time, inputs resident in HBM)
+    st0 = m.stats()
+    clocks = ClockSampler(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    clocks.start()
+    time.sleep(0.3)
+    m.profile(tnmps.PROF_CLASSES if args.profile_all else ("jacobi",))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize(device)
+    prof = m.profile_read()
+    m.profile(None)
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    st1 = m.stats()
+    m.check()
+    t_local = start.elapsed_time(end) / 1000.0
+    circ_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    exp_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    t = reduce_max(t_local, ws, device)
+    launches_step = (st1["launches"] - st0["launches"]) / args.steps
+    total_states = reduce_sum(B, ws, device) * args.steps
+    value = total_states * T / t
+    gates_per_s = total_states * 390 / t
+    full_per_step = st1["gates2q_full"]
+    # ---- dominant kernel: one-sided Jacobi (counters of the last step)
+    jac_ms, jac_n = prof["jacobi"]
+    alg_flops = 8 * st1["jacobi_pair_rows"] + 18 * st1["jacobi_rot_rows"]
+    exe_flops = 16 * st1["jacobi_pair_rows"] + 18 * st1["jacobi_rot_rows"]
+    launches_per_step_jac = jac_n / args.steps
+    avg_launch_s = jac_ms / 1000.0 / max(jac_n, 1)
+    per_launch_alg = alg_flops / max(launches_per_step_jac, 1)
+    achieved = per_launch_alg / avg_launch_s / 1e12
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if args.dtype == "c64":
+        peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peak_src = (f"derived: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                    f"{sm_max:.0f} MHz (max SM clock)")
+    else:
+        peak = FP64_NOMINAL_TFLOPS
+        peak_src = "nominal GB300 dense FP64 (1.25 TFLOP/s)"
+    roof = {"kernel": "k_jacobi (one-sided Jacobi SVD, K3)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": peak_src,
+            "executed_tflops": exe_flops / max(launches_per_step_jac, 1) / avg_launch_s / 1e12,
+            "alg_flops_per_launch": per_launch_alg, "avg_launch_ms": 1000 * avg_launch_s,
+            "share_of_step": jac_ms / args.steps / (1000 * t_local / args.steps),
+            "sweeps_per_svd": st1["jacobi_sweeps"] / max(st1["svds"], 1)}
+    # ---- end to end through the public host API (pinned host buffers)
+    th_pin = torch.tensor(th, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        m.reset()
+        m.apply_circuit(wl["circuit"], th_pin.numpy())
+        e_host = m.expect(ps)
+    t_e2e = reduce_max(time.perf_counter() - t0, ws, device)
+    e2e = {"value": reduce_sum(B, ws, device) * e2e_steps * T / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(B * P * 8), "d2h_bytes_per_step": int(B * 8),
+           "steps": e2e_steps}
+    assert np.all(np.isfinite(e_host))
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": config_dict(args, n, chi, B, P, T, m.arena.numel()),
+            "gates_per_s": gates_per_s,
+            "gates_chi128_per_s": reduce_sum(full_per_step, ws, device) * args.steps / t,
+            "phases_ms": {"circuit": circ_ms, "expect": exp_ms},
+            "expectations_per_s_sweep_phase": B * T / (exp_ms / 1000.0),
+            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches_step * args.steps),
+            "clocks": clk,
+        }
+        if args.profile_all:
+            line["class_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--dtype", choices=("c64", "c128"), default="c64")
+    ap.add_argument("--batch", type=int, default=304,
+                    help="theta rows per GPU (default 2 x 152 SMs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-all", action="store_true",
+                    help="time every kernel class with events (diagnostic; adds overhead)")
+    args = ap.parse_args()
+    args.rank_seed = 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -234,6 +234,7 @@ struct ProbGram {
   int k;
   static constexpr bool A_KFAST = false, B_KFAST = false;
   __device__ bool setup(int z, int &M_, int &N_, int &K_) {
+    if (blockIdx.y > blockIdx.x) return false;  // Hermitian: upper tiles only, mirrored
     k = dimv(v, z, l + 1);
     M_ = k;
     N_ = k;
@@ -251,7 +252,9 @@ struct ProbGram {
     return mkc<double>(u.re, u.im);
   }
   __device__ void store(int q, int r, cx<double> val) const {
-    E[(int64_t)q * k + r] = mkc<double>(val.re - (q == r ? 1.0 : 0.0), val.im);
+    const cx<double> e = mkc<double>(val.re - (q == r ? 1.0 : 0.0), val.im);
+    E[(int64_t)q * k + r] = e;
+    E[(int64_t)r * k + q] = cconj(e);
   }
 };
 
