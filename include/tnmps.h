@@ -214,6 +214,28 @@ tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, vo
                                   int lda, double *sigma_dev, int32_t *sweeps_dev,
                                   int max_sweeps, void *stream);
 
+/* ---- energies without any device allocation --------------------------------
+ * For callers that cannot call cudaMalloc -- code that runs under a device
+ * memory budget a host framework has already reserved in full, or a loop
+ * that must never enter the allocator. Same results and arguments as
+ * tnmps_expect_pauli_sum_dev without the workspace: the library uses its own
+ * scratch, a static device array of TNMPS_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits. The paper has no
+ * counterpart to this entry point.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - Term sets (with this context) needing more scratch than the array
+ *     holds for a single state are rejected with TNMPS_ERR_NOMEM and a
+ *     message giving both sizes. States are processed in chunks that fit.
+ *   - All calls share the array and each overwrites it (the term plan is
+ *     uploaded on every call); calls whose GPU work overlaps -- on other
+ *     streams or from other contexts -- race on it.
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *     call. Asynchronous on the context's stream. */
+#define TNMPS_NOALLOC_SCRATCH_BYTES (32u << 20)
+tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *ctx, const tnmps_terms *terms,
+                                            double *energy_dev, double *per_term_dev);
+
 /* Host-side fault injection for error-path tests: the call number `nth`
  * (counting from 1) of any state-changing entry point returns `status`
  * before touching the device. nth = 0 disarms. */

@@ -654,6 +654,16 @@ tnmps_status tnmps_expect_pauli_sum(tnmps_ctx *c, const tnmps_terms *t, void *ws
   return sync_check(c);
 }
 
+tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *c, const tnmps_terms *t,
+                                            double *energy_dev, double *per_term_dev) {
+  if (!c || !t || !energy_dev) return fail(c, TNMPS_ERR_ARG, "null argument");
+  if (t->plan.n != c->n) return fail(c, TNMPS_ERR_ARG, "term set built for another register");
+  tnmps_status st = inject(c);
+  if (st != TNMPS_OK) return st;
+  if ((st = move_centre(c, c->n - 1)) != TNMPS_OK) return st;
+  return expect_noalloc_impl(c, t->plan, t->gen, energy_dev, per_term_dev);
+}
+
 tnmps_status tnmps_check(tnmps_ctx *c) {
   if (!c) return TNMPS_ERR_ARG;
   return sync_check(c);

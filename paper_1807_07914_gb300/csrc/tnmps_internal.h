@@ -230,3 +230,5 @@ cudaError_t expect_run(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_byte
                        double *energy_dev, double *per_term_dev, double **energy_used,
                        double **per_term_used);
 size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk);
+tnmps_status expect_noalloc_impl(tnmps_ctx *c, const TermPlan &p, uint64_t gen,
+                                 double *energy_dev, double *per_term_dev);

@@ -83,6 +83,7 @@ def lib():
         "tnmps_last_error": (C.c_char_p, [P]),
         "tnmps_jacobi_svd_dev": (I, [I, I, I, I, P, I, P, P, I, P]),
         "tnmps_debug_inject": (I, [P, I, I]),
+        "tnmps_expect_pauli_sum_noalloc": (I, [P, P, P, P]),
         "tnmps_profile": (I, [P, C.c_uint32]),
         "tnmps_profile_read": (I, [P, P, P]),
     }
@@ -253,6 +254,12 @@ class MPSBatch:
         ws = self.workspace(terms, chunk)
         self._check(lib().tnmps_expect_pauli_sum_dev(self._h, terms._h, _ptr(ws), ws.numel(),
                                                      _ptr(energy), _ptr(per_term)))
+
+    def expect_noalloc(self, terms, energy, per_term=None):
+        """Like expect_dev, for callers that cannot allocate device memory:
+        the library's own static scratch replaces the workspace (asynchronous)."""
+        self._check(lib().tnmps_expect_pauli_sum_noalloc(self._h, terms._h, _ptr(energy),
+                                                         _ptr(per_term)))
 
     # -------------------------------------------------------------- inspection
     def check(self):
