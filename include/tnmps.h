@@ -236,6 +236,14 @@ tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, vo
 tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *ctx, const tnmps_terms *terms,
                                             double *energy_dev, double *per_term_dev);
 
+/* BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory):
+ * C[M x N] = A[M x K] * B[N x K]^T with A, B given as BF16 bit patterns
+ * (uint16), both K-major (row r of A at A + r*lda), C row-major FP32.
+ * K, lda, ldb multiples of 8; A, B 16-byte aligned. Asynchronous on
+ * `stream`. Used by the surrogate's layers; exported for unit parity. */
+tnmps_status tnmps_gemm_bf16_dev(int M, int N, int K, const uint16_t *A, int lda,
+                                 const uint16_t *B, int ldb, float *C, int ldc, void *stream);
+
 /* Host-side fault injection for error-path tests: the call number `nth`
  * (counting from 1) of any state-changing entry point returns `status`
  * before touching the device. nth = 0 disarms. */

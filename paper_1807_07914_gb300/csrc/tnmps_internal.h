@@ -50,6 +50,7 @@ __host__ __device__ __forceinline__ void cfma(cx<R> &acc, cx<R> a, cx<R> b) {
 // device error flag bits
 #define TNMPS_EFLAG_NOT_CONVERGED 1u
 #define TNMPS_EFLAG_NUMERIC 2u
+#define TNMPS_EFLAG_TIMEOUT 4u
 
 // device counter slots (uint64)
 enum {

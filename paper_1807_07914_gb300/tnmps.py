@@ -84,6 +84,7 @@ def lib():
         "tnmps_jacobi_svd_dev": (I, [I, I, I, I, P, I, P, P, I, P]),
         "tnmps_debug_inject": (I, [P, I, I]),
         "tnmps_expect_pauli_sum_noalloc": (I, [P, P, P, P]),
+        "tnmps_gemm_bf16_dev": (I, [I, I, I, P, I, P, I, P, I, P]),
         "tnmps_profile": (I, [P, C.c_uint32]),
         "tnmps_profile_read": (I, [P, P, P]),
     }
@@ -306,6 +307,21 @@ class MPSBatch:
 
     def inject(self, nth, status):
         self._check(lib().tnmps_debug_inject(self._h, int(nth), int(status)))
+
+
+def gemm_bf16(a, b, out=None, stream=None):
+    """C = A B^T on the tensor cores: a [M, K] and b [N, K] bfloat16 CUDA
+    tensors (K-major), result float32 [M, N]."""
+    assert a.dtype == torch.bfloat16 and b.dtype == torch.bfloat16 and a.is_cuda and b.is_cuda
+    M, K = a.shape
+    N = b.shape[0]
+    out = torch.empty((M, N), dtype=torch.float32, device=a.device) if out is None else out
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(a.device).cuda_stream
+    st = lib().tnmps_gemm_bf16_dev(M, N, K, _ptr(a), a.stride(0), _ptr(b), b.stride(0), _ptr(out),
+                                   out.stride(0), C.c_void_p(s))
+    if st != 0:
+        raise TnmpsError(st, "gemm_bf16 failed")
+    return out
 
 
 def jacobi_svd_dev(a, m, n, sigma, sweeps, max_sweeps=0, stream=None):
