@@ -244,6 +244,39 @@ tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *ctx, const tnmps_terms *t
 tnmps_status tnmps_gemm_bf16_dev(int M, int N, int K, const uint16_t *A, int lda,
                                  const uint16_t *B, int ldb, float *C, int ldc, void *stream);
 
+/* ---- learned surrogate of E(theta) -----------------------------------------
+ * MLP d_in -> width -> width -> 1 with SiLU (d_in, width multiples of 8),
+ * FP32 master weights, BF16 GEMMs on the tensor cores with FP32
+ * accumulation, last layer, elementwise work and Adam in FP32. The paper has
+ * no learned component; the surrogate proposes optimiser steps for the VQE
+ * loop of Sec. V.B and the MPS simulation verifies them. Parameters are a
+ * flat FP32 vector: W1 (width x d_in, row-major), b1, W2 (width x width),
+ * b2, w3 (width), b3. All pointers are device pointers; all calls are
+ * asynchronous on the surrogate's stream (tnmps_mlp_set_stream). */
+typedef struct tnmps_mlp tnmps_mlp;
+size_t tnmps_mlp_bytes(int d_in, int width, int max_batch);
+int64_t tnmps_mlp_num_params(int d_in, int width);
+tnmps_status tnmps_mlp_init(tnmps_mlp **out, int d_in, int width, int max_batch, void *arena,
+                            size_t arena_bytes);
+void tnmps_mlp_free(tnmps_mlp *mlp);
+tnmps_status tnmps_mlp_set_stream(tnmps_mlp *mlp, void *stream);
+const char *tnmps_mlp_last_error(const tnmps_mlp *mlp);
+/* copy parameters in (also clears the Adam moments) / out */
+tnmps_status tnmps_mlp_set_params(tnmps_mlp *mlp, const float *params_dev);
+tnmps_status tnmps_mlp_get_params(tnmps_mlp *mlp, float *params_dev);
+/* y[B] = f(x[B][d_in]) */
+tnmps_status tnmps_mlp_forward(tnmps_mlp *mlp, const float *x_dev, int B, float *y_dev);
+/* Forward + backward. With targets: loss = mean (y - t)^2 and its gradients;
+ * without (target_dev NULL): gradients of sum_b y_b, so grad_x[b] = dy_b/dx_b
+ * (the surrogate's gradient of E). Any output pointer may be NULL. */
+tnmps_status tnmps_mlp_backward(tnmps_mlp *mlp, const float *x_dev, const float *target_dev,
+                                int B, float *y_dev, float *loss_dev, float *grad_params_dev,
+                                float *grad_x_dev);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1) on
+ * the MSE loss of the batch. */
+tnmps_status tnmps_mlp_train_step(tnmps_mlp *mlp, const float *x_dev, const float *target_dev,
+                                  int B, float lr, int step, float *loss_dev);
+
 /* Host-side fault injection for error-path tests: the call number `nth`
  * (counting from 1) of any state-changing entry point returns `status`
  * before touching the device. nth = 0 disarms. */

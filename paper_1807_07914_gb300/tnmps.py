@@ -85,6 +85,17 @@ def lib():
         "tnmps_debug_inject": (I, [P, I, I]),
         "tnmps_expect_pauli_sum_noalloc": (I, [P, P, P, P]),
         "tnmps_gemm_bf16_dev": (I, [I, I, I, P, I, P, I, P, I, P]),
+        "tnmps_mlp_bytes": (S, [I, I, I]),
+        "tnmps_mlp_num_params": (C.c_int64, [I, I]),
+        "tnmps_mlp_init": (I, [C.POINTER(P), I, I, I, P, S]),
+        "tnmps_mlp_free": (None, [P]),
+        "tnmps_mlp_set_stream": (I, [P, P]),
+        "tnmps_mlp_last_error": (C.c_char_p, [P]),
+        "tnmps_mlp_set_params": (I, [P, P]),
+        "tnmps_mlp_get_params": (I, [P, P]),
+        "tnmps_mlp_forward": (I, [P, P, I, P]),
+        "tnmps_mlp_backward": (I, [P, P, P, I, P, P, P, P]),
+        "tnmps_mlp_train_step": (I, [P, P, P, I, C.c_float, I, P]),
         "tnmps_profile": (I, [P, C.c_uint32]),
         "tnmps_profile_read": (I, [P, P, P]),
     }
@@ -307,6 +318,75 @@ class MPSBatch:
 
     def inject(self, nth, status):
         self._check(lib().tnmps_debug_inject(self._h, int(nth), int(status)))
+
+
+class Surrogate:
+    """The MLP surrogate d_in -> width -> width -> 1 (SiLU) on one GPU."""
+
+    def __init__(self, d_in, width=256, max_batch=4096, device="cuda:0"):
+        L = lib()
+        self.device = torch.device(device)
+        self.d, self.w, self.max_batch = int(d_in), int(width), int(max_batch)
+        nb = L.tnmps_mlp_bytes(self.d, self.w, self.max_batch)
+        if nb == 0:
+            raise TnmpsError(1, "invalid surrogate sizes")
+        self.n_params = int(L.tnmps_mlp_num_params(self.d, self.w))
+        self.arena = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        st = L.tnmps_mlp_init(C.byref(h), self.d, self.w, self.max_batch, _ptr(self.arena), nb)
+        if st != 0:
+            raise TnmpsError(st, "surrogate init failed")
+        self._h = h
+        self._check(L.tnmps_mlp_set_stream(h, C.c_void_p(
+            torch.cuda.current_stream(self.device).cuda_stream)))
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.step = 0
+
+    def _check(self, st):
+        if st != 0:
+            raise TnmpsError(st, lib().tnmps_mlp_last_error(self._h).decode())
+
+    def set_params(self, p):
+        p = torch.as_tensor(p, dtype=torch.float32, device=self.device).contiguous()
+        assert p.numel() == self.n_params
+        self._check(lib().tnmps_mlp_set_params(self._h, _ptr(p)))
+        torch.cuda.current_stream(self.device).synchronize()
+        self.step = 0
+
+    def get_params(self):
+        p = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        self._check(lib().tnmps_mlp_get_params(self._h, _ptr(p)))
+        return p
+
+    def forward(self, x):
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=self.device)
+        self._check(lib().tnmps_mlp_forward(self._h, _ptr(x), x.shape[0], _ptr(y)))
+        return y
+
+    def backward(self, x, target=None, want_params=True, want_x=True):
+        x = x.contiguous()
+        B = x.shape[0]
+        y = torch.empty(B, dtype=torch.float32, device=self.device)
+        gp = torch.empty(self.n_params, dtype=torch.float32, device=self.device) if want_params else None
+        gx = torch.empty_like(x) if want_x else None
+        self._check(lib().tnmps_mlp_backward(self._h, _ptr(x), _ptr(target), B, _ptr(y),
+                                             _ptr(self.loss), _ptr(gp), _ptr(gx)))
+        return y, gp, gx
+
+    def train_step(self, x, target, lr):
+        self.step += 1
+        self._check(lib().tnmps_mlp_train_step(self._h, _ptr(x.contiguous()),
+                                               _ptr(target.contiguous()), x.shape[0],
+                                               float(lr), self.step, _ptr(self.loss)))
+        return self.loss
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tnmps_mlp_free(self._h)
+            self._h = None
+
+    __del__ = close
 
 
 def gemm_bf16(a, b, out=None, stream=None):
