@@ -214,6 +214,47 @@ tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, vo
                                   int lda, double *sigma_dev, int32_t *sweeps_dev,
                                   int max_sweeps, void *stream);
 
+/* ---- many circuits in one persistent launch --------------------------------
+ * Independent jobs with uneven register sizes, depths, bond caps and Pauli
+ * sums (the VQE loop of Sec. V.B run for many programs at once), complex64
+ * state and FP64 energies. One kernel launch runs every job: each CTA pulls
+ * whole jobs, most expensive first, and simulates them end to end.
+ * All job arrays are host memory, read by tnmps_batch_create only. */
+typedef struct {
+  int32_t n_qubits;           /* 2..256                                     */
+  int32_t chi_max;            /* 1..128                                     */
+  const tnmps_gate *gates;    /* gate list (as tnmps_apply_circuit)         */
+  int32_t n_gates;
+  const double *theta;        /* [n_params]                                 */
+  int32_t n_params;
+  const int32_t *term_off;    /* Pauli sum in CSR form (as tnmps_terms_create) */
+  const int32_t *sites;
+  const uint8_t *paulis;
+  const double *coeffs;
+  int32_t n_terms;
+} tnmps_job;
+typedef struct tnmps_batch tnmps_batch;
+/* Plan every job on the host (gate fusion, gauge moves, term tries). */
+tnmps_status tnmps_batch_create(tnmps_batch **out, const tnmps_job *jobs, int n_jobs,
+                                double cutoff);
+/* Device bytes for `ctas` persistent CTAs (one scratch slice each). */
+size_t tnmps_batch_bytes(const tnmps_batch *batch, int ctas);
+/* Upload the plan into `arena` (synchronous) and fix the launch shape:
+ * `ctas` CTAs of 256 threads, Jacobi column blocks of 16 or 32. */
+tnmps_status tnmps_batch_bind(tnmps_batch *batch, void *arena, size_t bytes, int ctas,
+                              int block_cols, void *stream);
+/* Capture the launch (work-counter reset + kernel) as a CUDA graph; later
+ * tnmps_batch_launch calls replay it. */
+tnmps_status tnmps_batch_capture_graph(tnmps_batch *batch);
+/* Enqueue the whole batch (asynchronous). */
+tnmps_status tnmps_batch_launch(tnmps_batch *batch);
+/* Synchronise; energies[n_jobs] (and per-job discarded weight, may be NULL). */
+tnmps_status tnmps_batch_results(tnmps_batch *batch, double *energy, double *discarded);
+tnmps_status tnmps_batch_info(const tnmps_batch *batch, int64_t *n_ops, int64_t *n_nodes,
+                              double *est_cost);
+const char *tnmps_batch_last_error(const tnmps_batch *batch);
+void tnmps_batch_free(tnmps_batch *batch);
+
 /* ---- energies without any device allocation --------------------------------
  * For callers that cannot call cudaMalloc -- code that runs under a device
  * memory budget a host framework has already reserved in full, or a loop

@@ -162,12 +162,6 @@ struct PGate {
   double angle, scale;
 };
 
-struct PlannedOp {
-  bool two;
-  Op2 o2;
-  Op1 o1;
-};
-
 Fac1 make_fac(const PGate &g, bool &fixed) {
   Fac1 f;
   memset(&f, 0, sizeof f);
@@ -214,21 +208,27 @@ void push_fac(std::vector<Fac1> &v, const Fac1 &f) {
   v.push_back(f);
 }
 
-tnmps_status plan_circuit(tnmps_ctx *c, const tnmps_gate *gates, size_t n_gates, size_t n_params,
-                          std::vector<PlannedOp> &out) {
-  const int n = c->n;
+}  // namespace
+
+// Plan a gate list for an n-qubit register (see tnmps_internal.h).
+tnmps_status plan_gates(int n, const tnmps_gate *gates, size_t n_gates, size_t n_params,
+                        std::vector<PlannedOp> &out, std::string &err) {
+  auto fail = [&](tnmps_status st, const char *msg) {
+    err = msg;
+    return st;
+  };
   // 1. validate and expand distant two-qubit gates into SWAP chains (Sec. IV)
   std::vector<PGate> ex;
   ex.reserve(n_gates);
   for (size_t k = 0; k < n_gates; ++k) {
     const tnmps_gate &g = gates[k];
     PGate p{g.op, g.q0, g.q1, g.param, g.angle, g.scale};
-    if (g.q0 < 0 || g.q0 >= n) return fail(c, TNMPS_ERR_ARG, "gate qubit out of range");
+    if (g.q0 < 0 || g.q0 >= n) return fail(TNMPS_ERR_ARG, "gate qubit out of range");
     if (g.param >= 0 && (size_t)g.param >= n_params)
-      return fail(c, TNMPS_ERR_ARG, "gate parameter index out of range");
+      return fail(TNMPS_ERR_ARG, "gate parameter index out of range");
     if (is_2q(g.op)) {
       if (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)
-        return fail(c, TNMPS_ERR_ARG, "bad two-qubit gate operands");
+        return fail(TNMPS_ERR_ARG, "bad two-qubit gate operands");
       const int step = g.q1 > g.q0 ? 1 : -1;
       int pos = g.q1;
       std::vector<PGate> chain;
@@ -243,7 +243,7 @@ tnmps_status plan_circuit(tnmps_ctx *c, const tnmps_gate *gates, size_t n_gates,
     } else if (is_1q(g.op)) {
       ex.push_back(p);
     } else {
-      return fail(c, TNMPS_ERR_UNSUPPORTED, "unknown gate opcode");
+      return fail(TNMPS_ERR_UNSUPPORTED, "unknown gate opcode");
     }
   }
   // 2. fuse single-qubit runs into the next two-qubit op on the site
@@ -292,6 +292,8 @@ tnmps_status plan_circuit(tnmps_ctx *c, const tnmps_gate *gates, size_t n_gates,
   return TNMPS_OK;
 }
 
+namespace {
+
 tnmps_status sync_check(tnmps_ctx *c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
@@ -326,7 +328,7 @@ tnmps_status move_centre(tnmps_ctx *c, int target) {
 tnmps_status run_circuit(tnmps_ctx *c, const tnmps_gate *gates, size_t n_gates,
                          const double *theta_dev, int64_t ths, size_t n_params) {
   std::vector<PlannedOp> ops;
-  tnmps_status st = plan_circuit(c, gates, n_gates, n_params, ops);
+  tnmps_status st = plan_gates(c->n, gates, n_gates, n_params, ops, c->last_error);
   if (st != TNMPS_OK) return st;
   for (const PlannedOp &po : ops) {
     if (po.two) {

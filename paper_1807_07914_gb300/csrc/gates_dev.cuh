@@ -75,3 +75,25 @@ __device__ __forceinline__ void op2_matrix(const Op2 &op, const double *theta, c
       G[4 * r + c] = acc;
     }
 }
+
+// Same as op2_matrix with the parts given separately (core 4x4 as 32
+// doubles, left and right factor lists).
+__device__ __forceinline__ void op2_matrix_parts(const double *core, const Fac1 *fl, int nl,
+                                                 const Fac1 *fr, int nr, const double *theta,
+                                                 cx<double> G[16]) {
+  cx<double> Ul[4], Ur[4];
+  side_matrix(fl, nl, theta, Ul);
+  side_matrix(fr, nr, theta, Ur);
+  cx<double> K[16];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c)
+      K[4 * r + c] = cmul(Ul[2 * (r >> 1) + (c >> 1)], Ur[2 * (r & 1) + (c & 1)]);
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      cx<double> acc = mkc<double>(0, 0);
+      for (int k = 0; k < 4; ++k)
+        acc = cadd(acc, cmul(mkc<double>(core[2 * (4 * r + k)], core[2 * (4 * r + k) + 1]),
+                             K[4 * k + c]));
+      G[4 * r + c] = acc;
+    }
+}

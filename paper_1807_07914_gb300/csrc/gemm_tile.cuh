@@ -23,12 +23,24 @@ struct GemmCfg<float> {
 //   cx<R> a(int i, int k) const, cx<R> b(int k, int j) const
 //   void store(int i, int j, cx<R> v) const
 //   static constexpr bool A_KFAST, B_KFAST  -- k is the contiguous index
+// One shared staging buffer for every instantiation of gemm_tile in a kernel
+// (a __shared__ array inside the template would be allocated once per
+// problem type).
+constexpr int GEMM_SMEM_BYTES = 2 * 16 * 33 * 16;  // max over precisions of 2 BK (BM+1) sizeof
+__device__ __forceinline__ unsigned char *gemm_smem() {
+  __shared__ __align__(16) unsigned char buf[GEMM_SMEM_BYTES];
+  return buf;
+}
+
 template <typename R, class P>
 __device__ __forceinline__ void gemm_tile(P &p, int M, int N, int K, int i0, int j0) {
   constexpr int BM = GemmCfg<R>::BM, BN = GemmCfg<R>::BN, BK = GemmCfg<R>::BK;
   constexpr int TM = BM / 16, TN = BN / 16;
-  __shared__ cx<R> As[BK][BM + 1];
-  __shared__ cx<R> Bs[BK][BN + 1];
+  static_assert(2 * BK * (BM + 1) * sizeof(cx<R>) <= GEMM_SMEM_BYTES, "gemm staging");
+  typedef cx<R> RowA[BM + 1];
+  typedef cx<R> RowB[BN + 1];
+  RowA *As = reinterpret_cast<RowA *>(gemm_smem());
+  RowB *Bs = reinterpret_cast<RowB *>(gemm_smem() + BK * (BM + 1) * sizeof(cx<R>));
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   cx<R> acc[TM][TN];

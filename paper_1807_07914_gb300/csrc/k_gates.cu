@@ -14,6 +14,7 @@
 // the column index of (s, c) is s*D + c. Theta is row-major (2 D_{l-1}) x
 // (2 D_{l+1}) in theta_buf; its column-major copy in w_buf is the Jacobi
 // input.
+#include "gate_dev.cuh"
 #include "gates_dev.cuh"
 #include "gemm_tile.cuh"
 #include "tnmps_internal.h"
@@ -91,24 +92,8 @@ __global__ void __launch_bounds__(256) k_apply_gate4(StateView v, Op2 op, const 
   __syncthreads();
   const int l = op.l;
   const int Dl = dimv(v, b, l), Dr = dimv(v, b, l + 2);
-  const int M = 2 * Dl, N = 2 * Dr;
-  cx<R> *T = tbuf + (int64_t)b * tw;
-  cx<R> *W = wbuf + (int64_t)b * tw;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Dl * Dr; e += gridDim.x * blockDim.x) {
-    const int a = e / Dr, c = e - a * Dr;
-    cx<R> x[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = T[(int64_t)(2 * a + (q >> 1)) * N + (q & 1) * Dr + c];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      cx<R> acc = mkc<R>(0, 0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) cfma(acc, G[4 * r + q], x[q]);
-      const int i = 2 * a + (r >> 1), j = (r & 1) * Dr + c;
-      T[(int64_t)i * N + j] = acc;
-      W[(int64_t)j * M + i] = acc;
-    }
-  }
+  gdev::apply_gate4_range<R>(G, tbuf + (int64_t)b * tw, wbuf + (int64_t)b * tw, Dl, Dr,
+                             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------- K4
@@ -120,77 +105,20 @@ __global__ void __launch_bounds__(256) k_split_select(StateView v, int l, const 
                                                       unsigned long long *counters) {
   const int b = blockIdx.x;
   const int Dl = dimv(v, b, l), Dm = dimv(v, b, l + 1), Dr = dimv(v, b, l + 2);
-  const int M = 2 * Dl, N = 2 * Dr;
-  const cx<R> *W = wbuf + (int64_t)b * tw;
-  __shared__ double sig[TNMPS_JACOBI_MAX_DIM];
-  __shared__ int perm[TNMPS_JACOBI_MAX_DIM];
-  __shared__ int s_k;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = warp; j < N; j += 8) {
-    double acc = 0;
-    for (int r = lane; r < M; r += 32) {
-      const cx<R> z = W[(int64_t)j * M + r];
-      acc += (double)z.re * z.re + (double)z.im * z.im;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sig[j] = sqrt(acc);
-  }
-  __syncthreads();
-  // stable descending rank
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const double sj = sig[j];
-    int rank = 0;
-    for (int i = 0; i < N; ++i) {
-      const double si = sig[i];
-      rank += (si > sj) || (si == sj && i < j);
-    }
-    perm[rank] = j;
-  }
-  __syncthreads();
+  // the Jacobi noise floor (8u of the norm) is always cut: columns below it
+  // were not orthogonalised
+  const double e_eff = eps > floor_eps ? eps : floor_eps;
+  double w;
+  bool bad;
+  const int k = gdev::select_cta<R>(wbuf + (int64_t)b * tw, 2 * Dl, 2 * Dr, cap, e_eff,
+                                    site_ptr<R>(v, b, l), &w, &bad);
   if (threadIdx.x == 0) {
-    double total = 0;
-    for (int r = 0; r < N; ++r) total += sig[perm[r]] * sig[perm[r]];
-    const double norm = sqrt(total);
-    const double smax = sig[perm[0]];
-    (void)smax;
-    // the Jacobi noise floor (8u of the norm) is always cut: columns below it
-    // were not orthogonalised
-    const double e_eff = eps > floor_eps ? eps : floor_eps;
-    const double thr = e_eff * norm;
-    int keep = 0;
-    while (keep < N && sig[perm[keep]] >= thr && sig[perm[keep]] > 0) ++keep;
-    int kmax = cap < M ? cap : M;
-    kmax = kmax < N ? kmax : N;
-    int k = keep < kmax ? keep : kmax;
-    if (k < 1) k = 1;
-    double kept = 0;
-    for (int r = 0; r < k; ++r) kept += sig[perm[r]] * sig[perm[r]];
-    double w = 0;
-    for (int r = k; r < N; ++r) w += sig[perm[r]] * sig[perm[r]];
-    if (!(total > 0) || !isfinite(total)) {
-      atomicOr(err, TNMPS_EFLAG_NUMERIC);
-      kept = 1;
-      w = 0;
-      total = 1;
-    }
-    discarded[b] += w / total;
-    scale[b] = 1.0 / sqrt(kept);
+    if (bad) atomicOr(err, TNMPS_EFLAG_NUMERIC);
+    discarded[b] += w;
+    scale[b] = 1.0;
     v.dims[(int64_t)b * (v.n + 1) + l + 1] = k;
-    s_k = k;
     atomicAdd(&counters[CNT_GATES2Q], 1ull);
     if (Dl == v.chi && Dm == v.chi && Dr == v.chi) atomicAdd(&counters[CNT_GATES2Q_FULL], 1ull);
-  }
-  __syncthreads();
-  const int k = s_k;
-  cx<R> *A = site_ptr<R>(v, b, l);  // (Dl, 2, k) == M x k row-major
-  for (int e = threadIdx.x; e < M * k; e += blockDim.x) {
-    const int i = e / k, r = e - i * k;
-    const int j = perm[r];
-    const double s = sig[j];
-    const R inv = s > 0 ? (R)(1.0 / s) : R(0);
-    const cx<R> z = W[(int64_t)j * M + i];
-    A[e] = mkc<R>(z.re * inv, z.im * inv);
   }
 }
 
@@ -304,20 +232,7 @@ __global__ void k_copy_u(StateView v, int l, const cx<float> *wbuf, int64_t tw) 
 template <typename R>
 __global__ void __launch_bounds__(256) k_normalise_site(StateView v, int site) {
   const int b = blockIdx.x;
-  const int cnt = dimv(v, b, site) * 2 * dimv(v, b, site + 1);
-  cx<R> *X = site_ptr<R>(v, b, site);
-  double acc = 0;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x)
-    acc += (double)X[e].re * X[e].re + (double)X[e].im * X[e].im;
-  __shared__ double red[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  double tot = 0;
-  for (int w = 0; w < 8; ++w) tot += red[w];
-  const R sc = tot > 0 ? (R)(1.0 / sqrt(tot)) : R(1);
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) X[e] = mkc<R>(X[e].re * sc, X[e].im * sc);
+  gdev::normalise_cta<R>(site_ptr<R>(v, b, site), dimv(v, b, site) * 2 * dimv(v, b, site + 1));
 }
 
 // ---------------------------------------------------------------- K1
@@ -348,134 +263,13 @@ __global__ void __launch_bounds__(256) k_gate1(StateView v, Op1 op, const double
 }
 
 // ---------------------------------------------------------------- K7
-template <typename R>
-__device__ __forceinline__ R block_sum(R v, R *red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  R t = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-  return t;
-}
-
-// In-place Householder QR of the column-major m x n matrix W (ld m):
-// afterwards R is the upper triangle and the reflector vectors (v_j with
-// implicit leading 1) sit below the diagonal; tau[j] holds their scalars
-// (H_j = I - tau_j v_j v_j^H, A = H_0 ... H_{r-1} R).
-template <typename R>
-__device__ void householder_qr(cx<R> *W, int m, int n, cx<R> *tau, R *red) {
-  const int r = m < n ? m : n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = 0; j < r; ++j) {
-    cx<R> *col = W + (int64_t)j * m;
-    R part = 0;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
-      part += col[i].re * col[i].re + col[i].im * col[i].im;
-    const R xn2 = block_sum(part, red);
-    const cx<R> alpha = col[j];
-    __syncthreads();
-    cx<R> tj = mkc<R>(0, 0);
-    if (!(xn2 == R(0) && alpha.im == R(0))) {
-      const R beta = -copysign(sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2), alpha.re);
-      tj = mkc<R>((beta - alpha.re) / beta, -alpha.im / beta);
-      // scal = 1 / (alpha - beta)
-      const R dr = alpha.re - beta, di = alpha.im;
-      const R den = dr * dr + di * di;
-      const cx<R> sc = mkc<R>(dr / den, -di / den);
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) col[i] = cmul(col[i], sc);
-      __syncthreads();
-      if (threadIdx.x == 0) col[j] = mkc<R>(beta, 0);
-    }
-    if (threadIdx.x == 0) tau[j] = tj;
-    __syncthreads();
-    if (tj.re == R(0) && tj.im == R(0)) continue;
-    // columns k > j:  x <- x - conj(tau) v (v^H x)
-    const cx<R> ct = cconj(tj);
-    for (int k = j + 1 + warp; k < n; k += nw) {
-      cx<R> *x = W + (int64_t)k * m;
-      cx<R> w = mkc<R>(0, 0);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : col[i];
-        cfma(w, cconj(vi), x[i]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
-        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
-      }
-      const cx<R> f = cmul(ct, w);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : col[i];
-        const cx<R> d = cmul(f, vi);
-        x[i] = mkc<R>(x[i].re - d.re, x[i].im - d.im);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Q = H_0 ... H_{r-1} [I; 0] (m x r, column-major ld m) from the reflectors in W.
-template <typename R>
-__device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *tau, cx<R> *Q) {
-  const int r = m < n ? m : n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
-    const int q = e / m, i = e - q * m;
-    Q[e] = mkc<R>(i == q ? R(1) : R(0), 0);
-  }
-  __syncthreads();
-  for (int j = r - 1; j >= 0; --j) {
-    const cx<R> tj = tau[j];
-    if (tj.re == R(0) && tj.im == R(0)) continue;
-    const cx<R> *v = W + (int64_t)j * m;
-    for (int q = j + warp; q < r; q += nw) {
-      cx<R> *x = Q + (int64_t)q * m;
-      cx<R> w = mkc<R>(0, 0);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : v[i];
-        cfma(w, cconj(vi), x[i]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
-        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
-      }
-      const cx<R> f = cmul(tj, w);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : v[i];
-        const cx<R> d = cmul(f, vi);
-        x[i] = mkc<R>(x[i].re - d.re, x[i].im - d.im);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // Right move at site c: C_c (2Dl x Dr) = Q R;  A_c <- Q;  R stays in w_buf.
 template <typename R>
 __global__ void __launch_bounds__(256) k_qr_right(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
                                                   int64_t tw, int32_t *newdim) {
   const int b = blockIdx.x;
-  const int Dl = dimv(v, b, c), Dr = dimv(v, b, c + 1);
-  const int m = 2 * Dl, n = Dr, r = m < n ? m : n;
-  cx<R> *W = wbuf + (int64_t)b * tw, *Q = tbuf + (int64_t)b * tw;
-  cx<R> *X = site_ptr<R>(v, b, c);
-  __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
-  __shared__ R red[32];
-  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
-    const int k = e / m, i = e - k * m;
-    W[e] = X[(int64_t)i * n + k];
-  }
-  __syncthreads();
-  householder_qr(W, m, n, tau, red);
-  householder_form_q(W, m, n, tau, Q);
-  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
-    const int i = e / r, q = e - i * r;
-    X[e] = Q[(int64_t)q * m + i];
-  }
+  const int r = gdev::qr_right_cta<R>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
+                                      wbuf + (int64_t)b * tw, tbuf + (int64_t)b * tw);
   if (threadIdx.x == 0) newdim[b] = r;
 }
 
@@ -485,17 +279,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_lq_left(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
                                                  int64_t tw, int32_t *newdim) {
   const int b = blockIdx.x;
-  const int Dl = dimv(v, b, c), Dr = dimv(v, b, c + 1);
-  const int m = 2 * Dr, n = Dl, r = m < n ? m : n;
-  cx<R> *W = wbuf + (int64_t)b * tw, *Q = tbuf + (int64_t)b * tw;
-  cx<R> *X = site_ptr<R>(v, b, c);
-  __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
-  __shared__ R red[32];
-  for (int e = threadIdx.x; e < m * n; e += blockDim.x) W[e] = cconj(X[e]);  // column k = conj row k
-  __syncthreads();
-  householder_qr(W, m, n, tau, red);
-  householder_form_q(W, m, n, tau, Q);
-  for (int e = threadIdx.x; e < r * m; e += blockDim.x) X[e] = cconj(Q[e]);
+  const int r = gdev::lq_left_cta<R>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
+                                     wbuf + (int64_t)b * tw, tbuf + (int64_t)b * tw);
   if (threadIdx.x == 0) newdim[b] = r;
 }
 

@@ -95,6 +95,18 @@ struct Op1 {
   Fac1 f[TNMPS_MAX_FAC];
 };
 
+// A planned op: fused two-qubit gate or standalone single-qubit op.
+struct PlannedOp {
+  bool two;
+  Op2 o2;
+  Op1 o1;
+};
+// Validate a gate list for an n-qubit register, expand distant two-qubit
+// gates into SWAP chains and fuse single-qubit runs into the next two-qubit
+// op on their site. On failure *err describes the problem.
+tnmps_status plan_gates(int n, const tnmps_gate *gates, size_t n_gates, size_t n_params,
+                        std::vector<PlannedOp> &out, std::string &err);
+
 // ---------------------------------------------------------------- layout
 // Device view of the batched MPS, passed by value to kernels.
 struct StateView {

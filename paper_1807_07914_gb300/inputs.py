@@ -98,13 +98,17 @@ def heisenberg_terms(n, rng, pbc=False):
 
 
 def random_pauli_terms(n, count, w_max, rng, scale_by_weight=False):
-    """``count`` distinct Pauli strings; weight w ~ U{1..w_max}, sites uniform
+    """``count`` distinct Pauli strings (at most as many as exist); weight
+    w ~ U{1..min(w_max, n)}, sites uniform
     without replacement, Paulis uniform over {X, Y, Z}, coefficients
     ~ N(0, 1) (divided by w when ``scale_by_weight``)."""
+    from math import comb
+    w_top = min(w_max, n)
+    count = min(count, sum(comb(n, w) * 3 ** w for w in range(1, w_top + 1)))
     seen = set()
     terms = []
     while len(terms) < count:
-        w = int(rng.integers(1, w_max + 1))
+        w = int(rng.integers(1, w_top + 1))
         sites = tuple(sorted(int(s) for s in rng.choice(n, size=w, replace=False)))
         paulis = tuple(int(p) for p in rng.integers(1, 4, size=w))
         key = (sites, paulis)
@@ -148,6 +152,24 @@ def terms_to_csr(terms):
         coeffs.append(float(c))
     return (np.asarray(off, dtype=np.int32), np.asarray(sites, dtype=np.int32),
             np.asarray(paulis, dtype=np.uint8), np.asarray(coeffs, dtype=np.float64))
+
+
+def batch_jobs(count, rng, n_range=(16, 64), depth_range=(2, 8), chi_range=(32, 128),
+               terms_range=(50, 2000), w_max=4):
+    """Heterogeneous job list: per job n ~ U{n_range}, ansatz depth ~ U{depth},
+    chi_max ~ U{chi_range}, Pauli sums of ~U{terms_range} strings of weight
+    <= w_max with coefficients ~ N(0, 1) / weight, theta ~ U(-pi, pi)."""
+    jobs = []
+    for _ in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        depth = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        chi = int(rng.integers(chi_range[0], chi_range[1] + 1))
+        T = int(rng.integers(terms_range[0], terms_range[1] + 1))
+        circ, P = hea_circuit(n, depth, ("RY", "RZ"))
+        jobs.append(dict(n=n, chi=chi, depth=depth, circuit=circ, n_params=P,
+                         theta=thetas(1, P, rng)[0],
+                         terms=random_pauli_terms(n, T, w_max, rng, scale_by_weight=True)))
+    return jobs
 
 
 # ---------------------------------------------------------------- workloads

@@ -32,6 +32,13 @@ class Gate(C.Structure):
                 ("angle", C.c_double), ("scale", C.c_double)]
 
 
+class Job(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("chi_max", C.c_int32), ("gates", C.c_void_p),
+                ("n_gates", C.c_int32), ("theta", C.c_void_p), ("n_params", C.c_int32),
+                ("term_off", C.c_void_p), ("sites", C.c_void_p), ("paulis", C.c_void_p),
+                ("coeffs", C.c_void_p), ("n_terms", C.c_int32)]
+
+
 class Stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("gates2q", "gates2q_full", "jacobi_pair_rows",
                                           "jacobi_rotations", "jacobi_sweeps", "svds",
@@ -96,6 +103,16 @@ def lib():
         "tnmps_mlp_forward": (I, [P, P, I, P]),
         "tnmps_mlp_backward": (I, [P, P, P, I, P, P, P, P]),
         "tnmps_mlp_train_step": (I, [P, P, P, I, C.c_float, I, P]),
+        "tnmps_batch_create": (I, [C.POINTER(P), P, I, D]),
+        "tnmps_batch_bytes": (S, [P, I]),
+        "tnmps_batch_bind": (I, [P, P, S, I, I, P]),
+        "tnmps_batch_capture_graph": (I, [P]),
+        "tnmps_batch_launch": (I, [P]),
+        "tnmps_batch_results": (I, [P, P, P]),
+        "tnmps_batch_info": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_double)]),
+        "tnmps_batch_last_error": (C.c_char_p, [P]),
+        "tnmps_batch_free": (None, [P]),
         "tnmps_profile": (I, [P, C.c_uint32]),
         "tnmps_profile_read": (I, [P, P, P]),
     }
@@ -384,6 +401,70 @@ class Surrogate:
     def close(self):
         if getattr(self, "_h", None):
             lib().tnmps_mlp_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class Batch:
+    """Many independent circuits (each: n, chi_max, gate list, theta, Pauli
+    sum) evaluated in one persistent launch (complex64 state, FP64 energies)."""
+
+    def __init__(self, jobs, cutoff=1e-10, ctas=None, block_cols=32, device="cuda:0"):
+        L = lib()
+        self.device = torch.device(device)
+        self._keep = []
+        arr = (Job * len(jobs))()
+        for i, jb in enumerate(jobs):
+            g = gate_array(jb["circuit"])
+            th = np.ascontiguousarray(np.asarray(jb["theta"], dtype=np.float64))
+            off, sites, paulis, coeffs = _csr(jb["terms"])
+            self._keep += [g, th, off, sites, paulis, coeffs]
+            arr[i] = Job(jb["n"], jb["chi"], C.cast(g, C.c_void_p), len(jb["circuit"]),
+                         th.ctypes.data, th.size, off.ctypes.data, sites.ctypes.data,
+                         paulis.ctypes.data, coeffs.ctypes.data, len(jb["terms"]))
+        h = C.c_void_p()
+        st = L.tnmps_batch_create(C.byref(h), arr, len(jobs), float(cutoff))
+        if st != 0:
+            raise TnmpsError(st, "batch planning failed")
+        self._h = h
+        self.n_jobs = len(jobs)
+        props = torch.cuda.get_device_properties(self.device)
+        self.ctas = ctas or props.multi_processor_count
+        nb = L.tnmps_batch_bytes(h, self.ctas)
+        self.arena = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self._check(L.tnmps_batch_bind(h, _ptr(self.arena), nb, self.ctas, block_cols,
+                                       C.c_void_p(self.stream.cuda_stream)))
+
+    def _check(self, st):
+        if st != 0:
+            raise TnmpsError(st, lib().tnmps_batch_last_error(self._h).decode())
+
+    def capture_graph(self):
+        self._check(lib().tnmps_batch_capture_graph(self._h))
+
+    def launch(self):
+        self._check(lib().tnmps_batch_launch(self._h))
+
+    def results(self):
+        e = np.zeros(self.n_jobs)
+        w = np.zeros(self.n_jobs)
+        self._check(lib().tnmps_batch_results(self._h, _ptr(e), _ptr(w)))
+        return e, w
+
+    def run(self):
+        self.launch()
+        return self.results()[0]
+
+    def info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_double()
+        lib().tnmps_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c))
+        return {"ops": a.value, "trie_nodes": b.value, "est_cost": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tnmps_batch_free(self._h)
             self._h = None
 
     __del__ = close
