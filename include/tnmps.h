@@ -57,8 +57,15 @@ typedef struct tnmps_terms tnmps_terms;
 
 /* Arithmetic of the state and of the contractions. TNMPS_C128: complex128
  * everywhere (the plain FP64 form). TNMPS_C64: complex64 storage and FP32
- * contractions/rotations; the energy reduction stays FP64. */
-typedef enum { TNMPS_C128 = 0, TNMPS_C64 = 1 } tnmps_dtype;
+ * contractions/rotations; the energy reduction stays FP64.
+ * TNMPS_C64_BF16SPLIT: as TNMPS_C64, except that the transfer-matrix sweeps
+ * of the expectation values run on the tensor cores as split-precision
+ * complex products: every FP32 operand value is split into two BF16 values
+ * hi + lo and each real product is hi*hi + hi*lo + lo*hi, accumulated in
+ * FP32 (relative rounding of order 2^-16 per product). Its state arena and
+ * circuit calls are those of TNMPS_C64; only the expectation workspace
+ * differs. */
+typedef enum { TNMPS_C128 = 0, TNMPS_C64 = 1, TNMPS_C64_BF16SPLIT = 2 } tnmps_dtype;
 
 typedef enum {
   TNMPS_OK = 0,

@@ -26,7 +26,7 @@ std::atomic<uint64_t> g_plan_gen{1};
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool valid_dtype(int d) { return d == TNMPS_C128 || d == TNMPS_C64; }
+bool valid_dtype(int d) { return d == TNMPS_C128 || d == TNMPS_C64 || d == TNMPS_C64_BF16SPLIT; }
 
 // bond capacities: cap[i] bounds D_{i-1} (dims index i), cap[0] = cap[n] = 1
 std::vector<int> bond_caps(int n, int chi) {
@@ -85,7 +85,7 @@ Layout make_layout(int n, int chi, int dtype, int batch, int max_params) {
   L.counters = p;
   p = al256(p + 8 * CNT_NUM);
   L.ebuf = p;
-  if (dtype == TNMPS_C64) p = al256(p + 16 * (size_t)batch * chi * chi);
+  if (dtype != TNMPS_C128) p = al256(p + 16 * (size_t)batch * chi * chi);
   L.total = p;
   return L;
 }

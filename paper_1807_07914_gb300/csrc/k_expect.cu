@@ -16,7 +16,10 @@
 // (start site, Pauli word); one transfer update per trie node serves every
 // term sharing that prefix. Nodes are processed level by level, batched over
 // nodes and states; each update is two complex GEMMs on the tiled core.
+#include <algorithm>
+
 #include "gemm_tile.cuh"
+#include "sweep_tc.h"
 #include "tnmps_internal.h"
 
 namespace {
@@ -244,7 +247,26 @@ struct WsLayout {
   int64_t renv_elems, env_elems, tmp_elems;
   // plan sub-offsets
   size_t o_site, o_parent, o_pauli, o_tterm, o_tnode, o_tsite, o_ident, o_coeffs;
+  // tensor-core form: site operand offsets/geometry, converted site operands,
+  // row-K environments (lprev/lcur) and intermediates (tmp) in bytes
+  bool tc;
+  size_t o_tc_soff, o_tc_geo, tc_sites_off;
+  int64_t tc_site_stride, tc_env_bytes;
 };
+
+static bool tc_form(const tnmps_ctx *c) { return c->dtype == TNMPS_C64_BF16SPLIT; }
+
+// byte offset of each site's converted operands inside one state's block
+static std::vector<int64_t> tc_site_offsets(const tnmps_ctx *c, int64_t *stride) {
+  std::vector<int64_t> off(c->n);
+  int64_t o = 0;
+  for (int i = 0; i < c->n; ++i) {
+    off[i] = o;
+    o += swtc::site_bytes(c->cap[i], c->cap[i + 1]);
+  }
+  *stride = o;
+  return off;
+}
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -276,6 +298,11 @@ static WsLayout layout(const tnmps_ctx *c, const TermPlan &p, int bc) {
   o = al(o + 8 * (size_t)c->batch);
   L.roff_off = o;
   o = al(o + 8 * (size_t)c->n);
+  // (kept ahead of every chunk-dependent region: the plan upload is cached)
+  L.o_tc_soff = o;
+  o = al(o + 8 * (size_t)c->n);
+  L.o_tc_geo = o;
+  o = al(o + 8 * (size_t)c->n);
   int64_t re = 0;
   for (int i = 0; i < c->n; ++i) re += (int64_t)c->cap[i + 1] * c->cap[i + 1];
   L.renv_elems = re;
@@ -284,14 +311,75 @@ static WsLayout layout(const tnmps_ctx *c, const TermPlan &p, int bc) {
   L.renv_off = o;
   o = al(o + esz * (size_t)bc * (size_t)re);
   const size_t ln = p.max_level_nodes > 0 ? (size_t)p.max_level_nodes : 1;
-  L.lprev_off = o;
-  o = al(o + esz * ln * bc * (size_t)L.env_elems);
-  L.lcur_off = o;
-  o = al(o + esz * ln * bc * (size_t)L.env_elems);
-  L.tmp_off = o;
-  o = al(o + esz * ln * bc * (size_t)L.tmp_elems);
+  L.tc = tc_form(c);
+  if (L.tc) {
+    L.tc_env_bytes = swtc::rowk_bytes(c->chi);
+    tc_site_offsets(c, &L.tc_site_stride);
+    L.tc_sites_off = o;
+    o = al(o + (size_t)bc * (size_t)L.tc_site_stride);
+    L.lprev_off = o;
+    o = al(o + ln * bc * (size_t)L.tc_env_bytes);
+    L.lcur_off = o;
+    o = al(o + ln * bc * (size_t)L.tc_env_bytes);
+    L.tmp_off = o;
+    o = al(o + ln * bc * 2 * (size_t)L.tc_env_bytes);
+  } else {
+    L.lprev_off = o;
+    o = al(o + esz * ln * bc * (size_t)L.env_elems);
+    L.lcur_off = o;
+    o = al(o + esz * ln * bc * (size_t)L.env_elems);
+    L.tmp_off = o;
+    o = al(o + esz * ln * bc * (size_t)L.tmp_elems);
+  }
   L.total = o;
   return L;
+}
+
+// The trie levels of one state chunk on the tensor cores (BF16-split form):
+// convert the site tensors, seed the roots with identity environments, then
+// per level the two GEMM steps and the dots of the terms ending there.
+static cudaError_t run_levels_tc(tnmps_ctx *c, const TermPlan &p, const WsLayout &L, char *ws,
+                                 const EnvBufs &e, const int32_t *d_site, const int32_t *d_parent,
+                                 const int32_t *d_pauli, const int32_t *d_tterm,
+                                 const int32_t *d_tnode, const int32_t *d_tsite, double *per_term) {
+  cudaStream_t st = c->stream;
+  TcSweep t{};
+  t.dims = c->dims;
+  t.n = c->n;
+  t.b0 = e.b0;
+  t.nb = e.nb;
+  t.site_ops = reinterpret_cast<uint8_t *>(ws + L.tc_sites_off);
+  t.site_off = reinterpret_cast<const int64_t *>(ws + L.o_tc_soff);
+  t.site_geo = reinterpret_cast<const int32_t *>(ws + L.o_tc_geo);
+  t.site_stride = L.tc_site_stride;
+  t.lprev = reinterpret_cast<uint8_t *>(ws + L.lprev_off);
+  t.lcur = reinterpret_cast<uint8_t *>(ws + L.lcur_off);
+  t.tbuf = reinterpret_cast<uint8_t *>(ws + L.tmp_off);
+  t.env_bytes = L.tc_env_bytes;
+  t.rt = swtc::cdiv(c->chi, 128);
+  t.nmax = c->chi <= 128 ? 128 : 256;
+  t.err = c->err;
+  cudaError_t err = tc_prep_sites(t, c->sites, c->site_off_dev, c->state_elems, st, &c->launches);
+  if (err != cudaSuccess) return err;
+  for (int d = 1; d <= p.depth; ++d) {
+    const int64_t s0 = p.level_start[d - 1], s1 = p.level_start[d];
+    const int nodes = (int)(s1 - s0);
+    if (nodes == 0) continue;
+    int dmax_r = 1;
+    for (int64_t k = s0; k < s1; ++k) dmax_r = std::max(dmax_r, c->ub[p.node_site[k] + 1]);
+    if (d == 1 && (err = tc_root_envs(t, d_site + s0, nodes, 0, st, &c->launches)) != cudaSuccess)
+      return err;
+    if ((err = tc_level(t, d_site + s0, d_parent + s0, d_pauli + s0, nodes, d == 1, dmax_r,
+                        c->counters, st, &c->launches)) != cudaSuccess)
+      return err;
+    const int64_t t0 = p.tlevel_start[d - 1], t1 = p.tlevel_start[d];
+    if ((err = tc_term_dot(t, e.renv, e.roff, e.renv_elems, d_tterm + t0, d_tnode + t0,
+                           d_tsite + t0, (int)(t1 - t0), p.n_terms, per_term, st,
+                           &c->launches)) != cudaSuccess)
+      return err;
+    std::swap(t.lprev, t.lcur);
+  }
+  return cudaSuccess;
 }
 
 template <typename R>
@@ -332,6 +420,19 @@ cudaError_t run_expect(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_byte
       o += (int64_t)c->cap[i + 1] * c->cap[i + 1];
     }
     UP(L.roff_off, roff);
+    std::vector<int64_t> tc_soff;
+    std::vector<int32_t> tc_geo;
+    if (L.tc) {
+      int64_t stride = 0;
+      tc_soff = tc_site_offsets(c, &stride);
+      tc_geo.resize(2 * (size_t)c->n);
+      for (int i = 0; i < c->n; ++i) {
+        tc_geo[2 * i] = swtc::cdiv(c->cap[i], swtc::KCH);
+        tc_geo[2 * i + 1] = swtc::cdiv(c->cap[i + 1], 64);
+      }
+      UP(L.o_tc_soff, tc_soff);
+      UP(L.o_tc_geo, tc_geo);
+    }
 #undef UP
     // pageable sources: make sure the staging finished before the vectors die
     if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
@@ -384,6 +485,13 @@ cudaError_t run_expect(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_byte
       pr.counters = c->counters;
       if ((err = launch_gemm<R>(pr, c->ub[i + 1], c->ub[i + 1], e.nb, st, &c->launches)) != cudaSuccess)
         return err;
+    }
+    if (L.tc) {
+      if ((err = run_levels_tc(c, p, L, ws, e, d_site, d_parent, d_pauli, d_tterm, d_tnode,
+                               d_tsite, per_term)) != cudaSuccess)
+        return err;
+      prof_end(c, PC_ENV, ev);
+      continue;
     }
     for (int d = 1; d <= p.depth; ++d) {
       const int64_t s0 = p.level_start[d - 1], s1 = p.level_start[d];

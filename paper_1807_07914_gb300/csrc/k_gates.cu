@@ -403,7 +403,7 @@ cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
   // K4: rank, A_l <- U_k, [orthonormalise U_k], C_{l+1} <- U_k^H Theta, normalise
   ev = prof_begin(c, PC_SPLIT);
   const double floor_eps =
-      c->dtype == TNMPS_C64 ? 8.0 * 5.9604644775390625e-08 : 8.0 * 1.1102230246251565e-16;
+      c->dtype != TNMPS_C128 ? 8.0 * 5.9604644775390625e-08 : 8.0 * 1.1102230246251565e-16;
   k_split_select<R><<<c->batch, 256, 0, c->stream>>>(v, l, wb, c->tw, c->eps, floor_eps,
                                                       c->cap[l + 1], c->discarded, c->scale,
                                                       c->err, c->counters);

@@ -1,7 +1,9 @@
 // Blackwell (sm_100 family) tensor-core helpers in inline PTX: tcgen05 MMA
 // with a TMEM accumulator, shared-memory matrix descriptors, mbarriers with
-// bounded waits, and TMEM load/alloc. Only the forms used here are wrapped.
+// bounded waits, bulk (TMA) copies, and TMEM load/alloc. Only the forms used
+// here are wrapped.
 #pragma once
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "tnmps_internal.h"
@@ -39,6 +41,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
     if (clock64() - t0 > max_cycles) return false;
   }
   return true;
+}
+
+// one arrival that also raises the barrier's expected transaction bytes
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// ---------------------------------------------------------------- bulk copy
+// Global -> shared bulk copy by the TMA unit (both addresses 16-byte
+// aligned, bytes a multiple of 16); completion is counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------- BF16 split
+// v = hi + lo + O(2^-17 |v|): hi = bf16(v), lo = bf16(v - hi), both RN.
+__device__ __forceinline__ void bf16_split(float v, uint16_t &hi, uint16_t &lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(l);
 }
 
 // ---------------------------------------------------------------- fences

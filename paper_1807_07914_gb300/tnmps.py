@@ -16,7 +16,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 OPS = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "RX": 8, "RY": 9,
        "RZ": 10, "CNOT": 16, "CZ": 17, "SWAP": 18}
-DTYPES = {"c128": 0, "c64": 1}
+DTYPES = {"c128": 0, "c64": 1, "c64_bf16split": 2}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOMEM", 3: "ERR_UNSUPPORTED", 4: "ERR_NOT_CONVERGED",
           5: "ERR_NUMERIC", 6: "ERR_CUDA", 7: "ERR_INJECTED"}
 
