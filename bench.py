@@ -11,9 +11,11 @@ Prints ONE JSON line. ``value`` = Pauli-term expectations per second
 (whole job: states x terms / step time, the state simulation included);
 ``gates_per_s`` = two-qubit gate applications per second; the dominant
 kernel's roofline (the one-sided Jacobi SVD) is measured live with CUDA
-events on the library's stream.
+events on the library's stream. ``random_terms`` reports the metric's second
+term set (2000 random strings of weight <= 4) as one expectation pass over
+the final states, with the tensor-core sweep kernel's roofline.
 
-  python bench.py [--gpus N --steps K --warmup W] [--dtype c64|c128] [--batch B]
+  python bench.py [--gpus N --steps K --warmup W] [--dtype c64_bf16split|c64|c128] [--batch B]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 Under torchrun each rank simulates its own batch (replicas; weak scaling).
 """
@@ -210,6 +212,50 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def random_terms_pass(args, m, wl, energy, stream, ws, device):
+    """One timed expectation pass of the 2000 random strings over the batch's
+    final states; the environment updates' algorithmic flops come from the
+    library's counters and the sweep GEMMs are event-timed on its stream."""
+    import torch
+    from paper_1807_07914_gb300 import tnmps
+    ps = tnmps.PauliSum(wl["n"], wl["terms_random"])
+    T = len(wl["terms_random"])
+    m.expect_dev(ps, energy, chunk=args.random_chunk)       # warm-up: workspace, plan upload
+    torch.cuda.synchronize(device)
+    s0 = m.stats()
+    m.profile(("env", "env_tc"))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.expect_dev(ps, energy, chunk=args.random_chunk)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    prof = m.profile_read()
+    m.profile(None)
+    s1 = m.stats()
+    m.check()
+    t = reduce_max(e0.elapsed_time(e1) / 1000.0, ws, device)
+    flops = s1["env_flops"] - s0["env_flops"]
+    out = {"terms": T, "weight_max": 4, "chunk": args.random_chunk,
+           "value": reduce_sum(m.batch, ws, device) * T / t, "unit": UNIT, "ms_per_pass": 1000 * t,
+           "env_updates": s1["env_updates"] - s0["env_updates"],
+           "env_alg_tflops": flops / t / 1e12}
+    peaks = load_peaks()
+    if args.dtype == "c64_bf16split":
+        tc_ms = prof["env_tc"][0]
+        alg = flops / (tc_ms / 1000.0) / 1e12
+        peak = float(peaks.get("bf16_tflops", 1933.1))
+        out["roofline"] = {
+            "kernel": "k_swtc (transfer-sweep GEMM steps on tcgen05, BF16 split)",
+            "bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s",
+            "frac": alg / peak, "traffic": None, "gemm_ms": tc_ms,
+            "executed_tflops": 3 * alg, "executed_frac": 3 * alg / peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+            "note": "achieved = algorithmic complex-GEMM flops (4 real MACs per complex MAC); "
+                    "executed = 3 x (hi*hi + hi*lo + lo*hi), padding to 32-wide tiles not counted"}
+    return out
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_setup()
@@ -297,7 +343,7 @@ def run_gpu(args):
     achieved = per_launch_alg / avg_launch_s / 1e12
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    if args.dtype == "c64":
+    if args.dtype != "c128":
         peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         peak_src = (f"derived: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                     f"{sm_max:.0f} MHz (max SM clock)")
@@ -325,6 +371,10 @@ def run_gpu(args):
            "h2d_bytes_per_step": int(B * P * 8), "d2h_bytes_per_step": int(B * 8),
            "steps": e2e_steps}
     assert np.all(np.isfinite(e_host))
+    # ---- the second term set of the metric: 2000 random strings of weight <= 4
+    # on the final states (expectation phase alone, states resident)
+    rand = None if args.no_random_terms else random_terms_pass(args, m, wl, energy, stream, ws,
+                                                                device)
     line = None
     if rank == 0:
         line = {
@@ -340,6 +390,8 @@ def run_gpu(args):
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches_step * args.steps),
             "clocks": clk,
         }
+        if rand is not None:
+            line["random_terms"] = rand
         if args.profile_all:
             line["class_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
         if not args.no_cpu_baseline:
@@ -358,7 +410,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
-    ap.add_argument("--dtype", choices=("c64", "c128"), default="c64")
+    ap.add_argument("--dtype", choices=("c64_bf16split", "c64", "c128"), default="c64_bf16split",
+                    help="c64_bf16split: complex64 state, FP32 Jacobi with FP64 Gram, sweeps on "
+                         "the tensor cores (BF16 split); c64: FP32 CUDA-core sweeps; c128: FP64")
+    ap.add_argument("--no-random-terms", action="store_true",
+                    help="skip the pass over the 2000 random strings")
+    ap.add_argument("--random-chunk", type=int, default=32,
+                    help="states per expectation chunk of the random-string pass")
     ap.add_argument("--batch", type=int, default=304,
                     help="theta rows per GPU (default 2 x 152 SMs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -116,7 +116,9 @@ typedef enum {
   TNMPS_PROF_GATE1 = 4,   /* standalone single-qubit gates (K1)                 */
   TNMPS_PROF_ENV = 5,     /* transfer-matrix environment updates (K5)           */
   TNMPS_PROF_TERM = 6,    /* term values and energy reduction (K6)              */
-  TNMPS_PROF_NUM = 7
+  TNMPS_PROF_ENV_TC = 7,  /* tensor-core GEMM steps of the K5 sweeps (BF16-split
+                             form; nested inside TNMPS_PROF_ENV)                */
+  TNMPS_PROF_NUM = 8
 } tnmps_prof_class;
 
 const char *tnmps_status_string(tnmps_status s);

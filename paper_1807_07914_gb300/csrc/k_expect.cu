@@ -369,9 +369,11 @@ static cudaError_t run_levels_tc(tnmps_ctx *c, const TermPlan &p, const WsLayout
     for (int64_t k = s0; k < s1; ++k) dmax_r = std::max(dmax_r, c->ub[p.node_site[k] + 1]);
     if (d == 1 && (err = tc_root_envs(t, d_site + s0, nodes, 0, st, &c->launches)) != cudaSuccess)
       return err;
+    cudaEvent_t ev = prof_begin(c, PC_ENV_TC);
     if ((err = tc_level(t, d_site + s0, d_parent + s0, d_pauli + s0, nodes, d == 1, dmax_r,
                         c->counters, st, &c->launches)) != cudaSuccess)
       return err;
+    prof_end(c, PC_ENV_TC, ev);
     const int64_t t0 = p.tlevel_start[d - 1], t1 = p.tlevel_start[d];
     if ((err = tc_term_dot(t, e.renv, e.roff, e.renv_elems, d_tterm + t0, d_tnode + t0,
                            d_tsite + t0, (int)(t1 - t0), p.n_terms, per_term, st,

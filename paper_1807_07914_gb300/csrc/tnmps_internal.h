@@ -67,7 +67,7 @@ enum {
 };
 
 // kernel classes for event timing (mirrors tnmps_prof_class in tnmps.h)
-enum { PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_NUM };
+enum { PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_ENV_TC, PC_NUM };
 
 // ---------------------------------------------------------------- ops
 // A single-qubit factor: fixed 2x2 (kind 0, row-major complex in m[]) or a

@@ -2,11 +2,14 @@
 
   python -m paper_1807_07914_gb300.prof_case jacobi --dtype c64 --batch 304 --m 256 --n 256
   python -m paper_1807_07914_gb300.prof_case circuit --dtype c64 --batch 152 --layers 9
+  python -m paper_1807_07914_gb300.prof_case sweep --dtype c64_bf16split --batch 8 --terms 2000
 
 ``jacobi`` runs the standalone batched SVD on random complex matrices (the
 shape of a saturated chi=128 two-site block) ``--reps`` times; ``circuit``
-runs the chi=128 ansatz on a reduced batch and then the Heisenberg energy.
-Both exit non-zero on any library error.
+runs the chi=128 ansatz on a reduced batch and then the Heisenberg energy;
+``sweep`` builds the chi=128 states (7 layers saturate the middle bonds) and
+then evaluates the first ``--terms`` of the 2000 random strings ``--reps``
+times (one state chunk). All exit non-zero on any library error.
 """
 import argparse
 import os
@@ -48,17 +51,34 @@ def circuit(a):
     print("energy[0]", e[0])
 
 
+def sweep(a):
+    wl = inputs.workload("chi128")
+    circ, P = inputs.hea_circuit(40, a.layers, ("RY", "RZ"))
+    m = tnmps.MPSBatch(40, 128, a.batch, dtype=a.dtype, max_params=P, eps=wl["eps"])
+    th = inputs.thetas(a.batch, P, inputs.rng_for(5, 7))
+    m.apply_circuit(circ, th)
+    ps = tnmps.PauliSum(40, wl["terms_random"][:a.terms])
+    energy = torch.empty(a.batch, dtype=torch.float64, device="cuda")
+    for _ in range(a.reps):
+        m.expect_dev(ps, energy, chunk=a.batch)
+    torch.cuda.synchronize()
+    m.check()
+    assert bool(torch.all(torch.isfinite(energy)))
+    print("energy[0]", float(energy[0]), "bonds", int(m.bond_dims().max()))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("jacobi", "circuit"))
-    ap.add_argument("--dtype", default="c64", choices=("c64", "c128"))
+    ap.add_argument("case", choices=("jacobi", "circuit", "sweep"))
+    ap.add_argument("--dtype", default="c64", choices=("c64", "c128", "c64_bf16split"))
+    ap.add_argument("--terms", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=152)
     ap.add_argument("--m", type=int, default=256)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--layers", type=int, default=9)
     a = ap.parse_args()
-    (jacobi if a.case == "jacobi" else circuit)(a)
+    {"jacobi": jacobi, "circuit": circuit, "sweep": sweep}[a.case](a)
 
 
 if __name__ == "__main__":

@@ -46,7 +46,7 @@ class Stats(C.Structure):
                                           "launches")]
 
 
-PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term")
+PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term", "env_tc")
 
 
 _lib = None
