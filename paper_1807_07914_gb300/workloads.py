@@ -1,0 +1,124 @@
+"""Measurements of the other workload shapes on one GPU, one JSON line each.
+
+  python -m paper_1807_07914_gb300.workloads large100 [--dtype c64_bf16split] [--oracle]
+  python -m paper_1807_07914_gb300.workloads rounds [--circuits 10] [--eps 1e-4] [--chi 64]
+
+``large100``: the 100-qubit single state (6 Ry/Rz + CNOT-ladder layers, 1200
+parameters, chi_max 256, cutoff 1e-8) and its 5000 random strings of weight
+<= 4: circuit time, expectation pass time, bond dimensions; with ``--oracle``
+the FP64 oracle is timed on the 20-term subset and its energy compared.
+
+``rounds``: the random-circuit workload of Sec. V.A (round 1 starts with H on
+every qubit; each round is a layer of random single-qubit gates followed by
+nearest-neighbour CNOTs), for 5..85 qubits in steps of 5 and 2..10 rounds in
+steps of 2, ``--circuits`` circuits each, at the paper's default cutoff 1e-4
+and a bond cap of ``--chi``: the largest bond dimension, the MPS storage in
+bytes (the paper's memory metric) and two-qubit gates per second (one circuit
+per launch sequence, so small registers are launch-latency bound).
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import inputs, tnmps
+
+ESIZE = {"c128": 16, "c64": 8, "c64_bf16split": 8}
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def large100(a):
+    wl = inputs.workload("large100")
+    th = torch.tensor(wl["thetas"][:1], dtype=torch.float64, device="cuda")
+    m = tnmps.MPSBatch(wl["n"], wl["chi_max"], 1, dtype=a.dtype, max_params=wl["n_params"],
+                       eps=wl["eps"])
+    gates = tnmps.gate_array(wl["circuit"])
+    ps = tnmps.PauliSum(wl["n"], wl["terms"])
+    energy = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):  # warm-up
+        m.reset()
+        m.apply_circuit_dev(gates, th)
+        m.expect_dev(ps, energy)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e2, e3 = _events()
+    m.reset()
+    s0 = m.stats()
+    e0.record()
+    m.apply_circuit_dev(gates, th)
+    e1.record()
+    e2.record()
+    m.expect_dev(ps, energy)
+    e3.record()
+    torch.cuda.synchronize()
+    m.check()
+    s1 = m.stats()
+    t_circ, t_exp = e0.elapsed_time(e1) / 1e3, e2.elapsed_time(e3) / 1e3
+    dims = m.bond_dims()[0]
+    out = {"workload": "large100: n=100, 6 layers Ry/Rz + CNOT ladder, chi_max 256, cutoff 1e-8, "
+                       "5000 strings of weight <= 4, 1 state",
+           "dtype": a.dtype, "circuit_s": t_circ, "expect_s": t_exp,
+           "expectations_per_s": len(wl["terms"]) / t_exp,
+           "env_alg_tflops": (s1["env_flops"] - s0["env_flops"]) / t_exp / 1e12,
+           "max_bond": int(dims.max()), "energy": float(energy[0])}
+    if a.oracle:
+        from oracle import energy as OE
+        sub = wl["terms"][:20]
+        t0 = time.perf_counter()
+        vals, _ = OE.term_values_mps(wl["n"], wl["circuit"], wl["thetas"][0], sub,
+                                     wl["chi_max"], wl["eps"])
+        t_or = time.perf_counter() - t0
+        e20, pt = m.expect(tnmps.PauliSum(wl["n"], sub), per_term=True)
+        out["oracle_20_terms_s"] = t_or
+        out["oracle_20_expectations_per_s"] = 20 / t_or
+        out["max_abs_dterm_20"] = float(np.max(np.abs(pt[0] - vals)))
+        out["dE_20_rel_sum_abs_c"] = float(abs(e20[0] - OE.energy_from_values(sub, vals)) /
+                                           sum(abs(t[0]) for t in sub))
+    print(json.dumps(out))
+
+
+def rounds(a):
+    res = []
+    for n in range(5, 90, 5):
+        for r in range(2, 12, 2):
+            maxb, bytes_, t, g2 = 0, [], 0.0, 0
+            for k in range(a.circuits):
+                rng = np.random.default_rng(10000 * n + 100 * r + k)
+                circ = inputs.rounds_circuit(n, r, rng)
+                m = tnmps.MPSBatch(n, a.chi, 1, dtype=a.dtype, max_params=0, eps=a.eps)
+                e0, e1 = _events()
+                e0.record()
+                m.apply_circuit(circ, None)
+                e1.record()
+                torch.cuda.synchronize()
+                m.check()
+                t += e0.elapsed_time(e1) / 1e3
+                g2 += sum(1 for gt in circ if gt[0] == "CNOT")
+                d = np.concatenate([[1], m.bond_dims()[0], [1]])
+                maxb = max(maxb, int(d.max()))
+                bytes_.append(int(np.sum(d[:-1] * 2 * d[1:])) * ESIZE[a.dtype])
+            res.append({"n": n, "rounds": r, "max_bond": maxb, "mps_bytes_mean": float(np.mean(bytes_)),
+                        "mps_bytes_max": int(np.max(bytes_)), "gates2q_per_s": g2 / t})
+    print(json.dumps({"workload": f"Sec. V.A rounds circuits, {a.circuits} per (n, rounds), "
+                                  f"cutoff {a.eps}, chi cap {a.chi}, {a.dtype}", "rows": res}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=("large100", "rounds"))
+    ap.add_argument("--dtype", default="c64_bf16split", choices=tuple(ESIZE))
+    ap.add_argument("--oracle", action="store_true")
+    ap.add_argument("--circuits", type=int, default=10)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--chi", type=int, default=64)
+    a = ap.parse_args()
+    (large100 if a.case == "large100" else rounds)(a)
+
+
+if __name__ == "__main__":
+    main()
