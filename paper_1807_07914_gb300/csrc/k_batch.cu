@@ -104,24 +104,34 @@ __device__ void cta_gemm(const P &p, int M, int N, int K, bool upper = false) {
   __syncthreads();
 }
 
-// E = U^H U - I, FP64 accumulation of the FP32 products, mirrored upper tiles
+// same, accumulating in FP32 within each K slice and in FP64 across slices
+template <class P>
+__device__ void cta_gemm_mixed(const P &p, int M, int N, int K, bool upper = false) {
+  constexpr int BM = GemmCfg<float>::BM, BN = GemmCfg<float>::BN;
+  P q = p;
+  for (int i0 = 0; i0 < M; i0 += BM)
+    for (int j0 = 0; j0 < N; j0 += BN)
+      if (!upper || i0 / BM <= j0 / BN) gemm_tile_mixed(q, M, N, K, i0, j0);
+  __syncthreads();
+}
+
+// E = U^H U - I (FP64 result, FP32 slice sums added in FP64), mirrored upper tiles
 struct GramP {
   const cx<float> *U;
   cx<double> *E;
   int k;
   static constexpr bool A_KFAST = false, B_KFAST = false;
-  __device__ cx<double> a(int q, int i) const {
-    const cx<float> u = U[(int64_t)i * k + q];
-    return mkc<double>(u.re, -(double)u.im);
-  }
-  __device__ cx<double> b(int i, int q) const {
-    const cx<float> u = U[(int64_t)i * k + q];
-    return mkc<double>(u.re, u.im);
-  }
+  __device__ cx<float> a(int q, int i) const { return cconj(U[(int64_t)i * k + q]); }
+  __device__ cx<float> b(int i, int q) const { return U[(int64_t)i * k + q]; }
+  // one writer per entry pair (upper triangle); the diagonal is real
   __device__ void store(int q, int r, cx<double> v) const {
-    const cx<double> e = mkc<double>(v.re - (q == r ? 1.0 : 0.0), v.im);
-    E[(int64_t)q * k + r] = e;
-    E[(int64_t)r * k + q] = cconj(e);
+    if (q > r) return;
+    if (q == r) {
+      E[(int64_t)q * k + q] = mkc<double>(v.re - 1.0, 0.0);
+      return;
+    }
+    E[(int64_t)q * k + r] = v;
+    E[(int64_t)r * k + q] = cconj(v);
   }
 };
 struct OrthoP {
@@ -230,9 +240,9 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
           break;
         }
         discarded += w;
-        // re-orthonormalise U_k with an FP64 Gram: U <- U (I - E/2)
+        // re-orthonormalise U_k with the FP64 Gram: U <- U (I - E/2)
         GramP pg{Cl, Eb, k};
-        cta_gemm<double>(pg, k, k, M, true);
+        cta_gemm_mixed(pg, k, k, M, true);
         OrthoP po{Cl, Eb, W, k};
         cta_gemm<R>(po, M, k, k);
         cta_copy<R>(Cl, W, (int64_t)M * k);

@@ -150,8 +150,9 @@ struct ProbSplit {
   __device__ void store(int r, int j, cx<R> val) const { C[(int64_t)r * N + j] = val; }
 };
 
-// complex64 form: E = U^H U - I with FP64 accumulation of the (exact) FP32
-// products -- the FP64 Gram of the orthogonalisation step
+// complex64 form: E = U^H U - I, the FP64 Gram of the orthogonalisation step:
+// FP32 FMAs within each 16-wide slice of K, slice sums added in FP64 (see
+// gemm_tile_mixed), which keeps the error near 1e-8 for unit columns
 struct ProbGram {
   StateView v;
   int l;
@@ -171,18 +172,19 @@ struct ProbGram {
     E = ebuf + (int64_t)z * estride;
     return true;
   }
-  __device__ cx<double> a(int q, int i) const {
-    const cx<float> u = U[(int64_t)i * k + q];
-    return mkc<double>(u.re, -(double)u.im);
-  }
-  __device__ cx<double> b(int i, int q) const {
-    const cx<float> u = U[(int64_t)i * k + q];
-    return mkc<double>(u.re, u.im);
-  }
+  __device__ cx<float> a(int q, int i) const { return cconj(U[(int64_t)i * k + q]); }
+  __device__ cx<float> b(int i, int q) const { return U[(int64_t)i * k + q]; }
+  // one writer per entry pair: the upper triangle stores both mirror
+  // entries (a diagonal tile also computes the lower ones, rounded
+  // differently); the diagonal of a Hermitian Gram is real
   __device__ void store(int q, int r, cx<double> val) const {
-    const cx<double> e = mkc<double>(val.re - (q == r ? 1.0 : 0.0), val.im);
-    E[(int64_t)q * k + r] = e;
-    E[(int64_t)r * k + q] = cconj(e);
+    if (q > r) return;
+    if (q == r) {
+      E[(int64_t)q * k + q] = mkc<double>(val.re - 1.0, 0.0);
+      return;
+    }
+    E[(int64_t)q * k + r] = val;
+    E[(int64_t)r * k + q] = cconj(val);
   }
 };
 
@@ -418,7 +420,7 @@ cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
     pg.l = l;
     pg.ebuf = reinterpret_cast<cx<double> *>(c->ebuf);
     pg.estride = (int64_t)c->chi * c->chi;
-    if ((e = launch_gemm<double>(pg, kub, kub, c->batch, c->stream, &c->launches)) != cudaSuccess)
+    if ((e = launch_gemm_mixed(pg, kub, kub, c->batch, c->stream, &c->launches)) != cudaSuccess)
       return e;
     ProbOrtho po{};
     po.v = v;
