@@ -25,14 +25,15 @@
 // each product is hi*hi + hi*lo + lo*hi (three MMAs; the dropped lo*lo term
 // is of relative size 2^-16), accumulated in FP32.
 //
-// Pipeline per CTA (128 threads): one thread of warp 0 streams each K step's
-// tiles (A hi/lo, B hi/lo) into a ring of shared-memory stages with bulk
-// copies on the TMA unit, counted on the stage's mbarrier; one thread of warp
-// 1 issues the stage's MMAs once it has landed and commits them to the stage's
-// "empty" mbarrier; then all four warps read the accumulator with tcgen05.ld
-// and write the split result. Every wait is bounded: after a timeout the CTA
-// flags TNMPS_EFLAG_TIMEOUT, waits (bounded) for its copies in flight, frees
-// its tensor memory and returns.
+// Pipeline: persistent CTAs (one per SM, 192 threads) walk the output tiles.
+// One thread streams each K step's tiles (A hi/lo, B hi/lo) into a ring of
+// shared-memory stages with bulk copies on the TMA unit, counted on the
+// stage's mbarrier; one thread issues the stage's MMAs into one of two TMEM
+// accumulators and commits them to the stage's "empty" mbarrier; four warps
+// read the other accumulator with tcgen05.ld and write the split result of
+// the previous tile meanwhile. Every wait is bounded: after a timeout the CTA
+// flags TNMPS_EFLAG_TIMEOUT, waits (bounded) for its copies and MMAs in
+// flight, frees its tensor memory and returns.
 #include "sweep_tc.h"
 #include "tc_util.cuh"
 
@@ -154,6 +155,7 @@ struct Unit {
   int row0;      // destination row of accumulator row 0 of the tile
   int half[2];   // K half of the destination for the Re / Im accumulator rows
   float sgn[2];
+  unsigned long long flops;  // algorithmic flops to count for this item (0: none)
 };
 
 struct LevelArgsTc {
@@ -168,13 +170,14 @@ struct LevelArgsTc {
 struct Step1 {
   TcSweep t;
   LevelArgsTc lv;
-  __device__ bool setup(Unit &u) const {
-    const int unit = blockIdx.x / lv.grid_m, g = blockIdx.x - unit * lv.grid_m;
+  __device__ bool setup(int item, Unit &u) const {
+    const int unit = item / lv.grid_m, g = item - unit * lv.grid_m;
     const int zb = unit / lv.nodes, node = unit - zb * lv.nodes;
     const int site = lv.site[node];
     const int Dl = dim_of(t, zb, site), Dr = dim_of(t, zb, site + 1);
     const int MT = dcdiv(Dr, 64);
     if (g >= 2 * MT) return false;
+    u.flops = 0;
     const int sp = g / MT, tt = g - sp * MT;
     const int mt_cap = t.site_geo[2 * site + 1];
     const uint8_t *base = t.site_ops + (int64_t)zb * t.site_stride + t.site_off[site];
@@ -211,8 +214,8 @@ struct Step1 {
 struct Step2 {
   TcSweep t;
   LevelArgsTc lv;
-  __device__ bool setup(Unit &u) const {
-    const int unit = blockIdx.x / lv.grid_m, g = blockIdx.x - unit * lv.grid_m;
+  __device__ bool setup(int item, Unit &u) const {
+    const int unit = item / lv.grid_m, g = item - unit * lv.grid_m;
     const int zb = unit / lv.nodes, node = unit - zb * lv.nodes;
     const int site = lv.site[node];
     const int Dl = dim_of(t, zb, site), Dr = dim_of(t, zb, site + 1);
@@ -237,14 +240,11 @@ struct Step2 {
     u.half[0] = 0;
     u.half[1] = 1;
     u.sgn[0] = u.sgn[1] = 1.f;
-    if (g == 0 && threadIdx.x == 0) {
-      // algorithmic flops of the update (the root's identity product is not counted)
-      const bool root = lv.level1;
-      atomicAdd(&lv.counters[CNT_ENV_UPDATES], 1ull);
-      atomicAdd(&lv.counters[CNT_ENV_FLOPS],
-                16ull * Dl * Dr * (unsigned long long)Dr +
-                    (root ? 0ull : 16ull * Dl * Dl * (unsigned long long)Dr));
-    }
+    // algorithmic flops of the whole update, counted once (M tile 0); the
+    // root's product with the identity is not counted
+    u.flops = g == 0 ? 16ull * Dl * Dr * (unsigned long long)Dr +
+                           (lv.level1 ? 0ull : 16ull * Dl * Dl * (unsigned long long)Dr)
+                     : 0ull;
     return true;
   }
 };
@@ -258,30 +258,55 @@ struct Ring {
   static constexpr int SMEM = 1024 + S * STAGE;
 };
 
+// Wait on an mbarrier phase unless another role of the CTA has failed; a
+// timeout marks the CTA failed. Returns true when the phase completed.
+__device__ __forceinline__ bool wait_or_fail(uint64_t *bar, uint32_t parity,
+                                             volatile int *fail) {
+  const long long t0 = clock64();
+  while (!tc::mbar_try_wait(bar, parity)) {
+    if (*fail) return false;
+    if (clock64() - t0 > 2000000000ll) {
+      *fail = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Persistent CTAs (one per SM) walk the items (node-state, M tile)
+// blockIdx.x, blockIdx.x + gridDim.x, ... with three roles:
+//   warp 4 (one thread): bulk copies of every K step of every item into the
+//     stage ring (a stage is refilled once the MMAs that read it completed);
+//   warp 5 (one thread): the MMAs of item i into accumulator i % 2, after the
+//     epilogue has drained that accumulator (item i - 2);
+//   warps 0-3: the epilogue of item i (warp w reads TMEM lanes 32w..32w+31),
+//     overlapping the MMAs of item i + 1.
 template <class Prob, int NMAX>
-__global__ void __launch_bounds__(128, 1) k_swtc(Prob p, uint32_t *err) {
+__global__ void __launch_bounds__(192, 1) k_swtc(Prob p, int items, uint32_t *err) {
   using RG = Ring<NMAX>;
   constexpr int S = RG::S;
   extern __shared__ uint8_t smraw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                             ~(uintptr_t)1023);
-  __shared__ uint64_t full[S], empty[S], done;
+  __shared__ uint64_t full[S], empty[S], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
-  Unit u;
-  if (!p.setup(u)) return;  // uniform over the CTA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t ntm = (uint32_t)NMAX;
+  constexpr uint32_t NTM = 2 * NMAX;  // two accumulators
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, ntm);
+    tc::tmem_alloc(&tmem_base, NTM);
     tc::tmem_relinquish();
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 32) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 4);
+    }
+    tc::mbar_init(&mma_done, 1);
     tc::mbar_fence_init();
     s_fail = 0;
   }
@@ -289,95 +314,136 @@ __global__ void __launch_bounds__(128, 1) k_swtc(Prob p, uint32_t *err) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
+  volatile int *fail = &s_fail;
 
-  if (warp == 0) {
-    if (lane == 0) {  // producer: bulk copies of the K steps into the ring
-      int issued = 0;
-      for (int kt = 0; kt < u.nk; ++kt) {
-        const int s = kt % S;
-        if (kt >= S && !tc::mbar_wait(&empty[s], (uint32_t)(((kt / S) - 1) & 1))) {
-          s_fail = 1;
-          break;
+  if (warp == 4) {
+    if (lane == 0) {  // producer
+      int kg = 0;     // K steps issued so far (all items)
+      for (int it = blockIdx.x; it < items && !*fail; it += gridDim.x) {
+        Unit u;
+        if (!p.setup(it, u)) continue;
+        for (int kt = 0; kt < u.nk; ++kt, ++kg) {
+          const int s = kg % S;
+          if (kg >= S && !wait_or_fail(&empty[s], (uint32_t)(((kg / S) - 1) & 1), fail)) break;
+          const int sh = kt / u.kc, q = kt - sh * u.kc;
+          const uint8_t *a = u.a + sh * u.a_s + q * u.a_kt;
+          const uint8_t *b = u.b + sh * u.b_s + q * u.b_kt;
+          uint8_t *st = sm + s * RG::STAGE;
+          tc::mbar_arrive_expect_tx(&full[s], 2 * RG::A_PIECE + 2 * u.b_bytes);
+          tc::bulk_g2s(st, a, RG::A_PIECE, &full[s]);
+          tc::bulk_g2s(st + RG::A_PIECE, a + u.a_pc, RG::A_PIECE, &full[s]);
+          tc::bulk_g2s(st + 2 * RG::A_PIECE, b, u.b_bytes, &full[s]);
+          tc::bulk_g2s(st + 2 * RG::A_PIECE + RG::B_PIECE, b + u.b_pc, u.b_bytes, &full[s]);
         }
-        const int sh = kt / u.kc, q = kt - sh * u.kc;
-        const uint8_t *a = u.a + sh * u.a_s + q * u.a_kt;
-        const uint8_t *b = u.b + sh * u.b_s + q * u.b_kt;
-        uint8_t *st = sm + s * RG::STAGE;
-        tc::mbar_arrive_expect_tx(&full[s], 2 * RG::A_PIECE + 2 * u.b_bytes);
-        tc::bulk_g2s(st, a, RG::A_PIECE, &full[s]);
-        tc::bulk_g2s(st + RG::A_PIECE, a + u.a_pc, RG::A_PIECE, &full[s]);
-        tc::bulk_g2s(st + 2 * RG::A_PIECE, b, u.b_bytes, &full[s]);
-        tc::bulk_g2s(st + 2 * RG::A_PIECE + RG::B_PIECE, b + u.b_pc, u.b_bytes, &full[s]);
-        issued = kt + 1;
       }
       // every copy issued must have landed before the CTA may leave
-      for (int kt = issued > S ? issued - S : 0; kt < issued; ++kt)
-        if (!tc::mbar_wait(&full[kt % S], (uint32_t)((kt / S) & 1))) s_fail = 1;
+      for (int k = kg > S ? kg - S : 0; k < kg; ++k)
+        if (!tc::mbar_wait(&full[k % S], (uint32_t)((k / S) & 1))) s_fail = 1;
     }
     __syncwarp();
-  } else if (warp == 1) {
+  } else if (warp == 5) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = tc::idesc_bf16(128, u.N);
-      for (int kt = 0; kt < u.nk; ++kt) {
-        const int s = kt % S;
-        if (!tc::mbar_wait(&full[s], (uint32_t)((kt / S) & 1))) {
-          s_fail = 1;
-          break;
-        }
+      int kg = 0, n = 0;  // K steps consumed, items started
+      for (int it = blockIdx.x; it < items && !*fail; it += gridDim.x) {
+        Unit u;
+        if (!p.setup(it, u)) continue;
+        const int ab = n & 1;
+        if (n >= 2 && !wait_or_fail(&acc_empty[ab], (uint32_t)(((n >> 1) - 1) & 1), fail)) break;
         tc::fence_after_sync();
-        const uint32_t a = tc::smem_u32(sm + s * RG::STAGE);
-        const uint32_t al = a + RG::A_PIECE, b = a + 2 * RG::A_PIECE, bl = b + RG::B_PIECE;
+        const uint32_t d = tmem + (uint32_t)(ab * NMAX);
+        const uint32_t idesc = tc::idesc_bf16(128, u.N);
+        bool ok = true;
+        for (int kt = 0; kt < u.nk; ++kt, ++kg) {
+          const int s = kg % S;
+          if (!wait_or_fail(&full[s], (uint32_t)((kg / S) & 1), fail)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t a = tc::smem_u32(sm + s * RG::STAGE);
+          const uint32_t al = a + RG::A_PIECE, b = a + 2 * RG::A_PIECE, bl = b + RG::B_PIECE;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint64_t ah = tc::smem_desc(a + j * 256, 128, 1024);
-          const uint64_t alo = tc::smem_desc(al + j * 256, 128, 1024);
-          const uint64_t bh = tc::smem_desc(b + j * 256, 128, 1024);
-          const uint64_t blo = tc::smem_desc(bl + j * 256, 128, 1024);
-          tc::mma_bf16(tmem, ah, bh, idesc, (kt > 0 || j > 0) ? 1u : 0u);
-          tc::mma_bf16(tmem, ah, blo, idesc, 1u);
-          tc::mma_bf16(tmem, alo, bh, idesc, 1u);
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t ah = tc::smem_desc(a + j * 256, 128, 1024);
+            const uint64_t alo = tc::smem_desc(al + j * 256, 128, 1024);
+            const uint64_t bh = tc::smem_desc(b + j * 256, 128, 1024);
+            const uint64_t blo = tc::smem_desc(bl + j * 256, 128, 1024);
+            tc::mma_bf16(d, ah, bh, idesc, (kt > 0 || j > 0) ? 1u : 0u);
+            tc::mma_bf16(d, ah, blo, idesc, 1u);
+            tc::mma_bf16(d, alo, bh, idesc, 1u);
+          }
+          tc::mma_commit(&empty[s]);
         }
-        tc::mma_commit(&empty[s]);
+        if (!ok) break;
+        tc::mma_commit(&acc_full[ab]);
+        if (u.flops) {
+          atomicAdd(&p.lv.counters[CNT_ENV_UPDATES], 1ull);
+          atomicAdd(&p.lv.counters[CNT_ENV_FLOPS], u.flops);
+        }
+        ++n;
       }
-      tc::mma_commit(&done);  // tracks every MMA issued above
+      // every MMA issued must have completed before the tensor memory is freed
+      tc::mma_commit(&mma_done);
+      if (!tc::mbar_wait(&mma_done, 0)) s_fail = 1;
     }
     __syncwarp();
-  }
-  if (!tc::mbar_wait(&done, 0)) s_fail = 1;
-  __syncthreads();
-  tc::fence_after_sync();
-  if (!s_fail) {
+  } else {  // epilogue warps 0-3
     const int part = warp >> 1;
-    const int row = u.row0 + (warp & 1) * 32 + lane;
-    const int kvb = (part ? u.half[1] : u.half[0]) * 4;
-    const float sg = part ? u.sgn[1] : u.sgn[0];
-    uint8_t *rt0 = u.out + (int64_t)(row >> 7) * TILE;
-    const int64_t rt_stride = (int64_t)((p.t.rt)) * TILE;  // next piece
-    for (int c = 0; c < u.N; c += 32) {
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      uint8_t *hi = rt0 + (int64_t)(c / KCH) * 2 * rt_stride;
+    int n = 0;
+    for (int it = blockIdx.x; it < items && !*fail; it += gridDim.x) {
+      Unit u;
+      if (!p.setup(it, u)) continue;
+      const int ab = n & 1;
+      if (!wait_or_fail(&acc_full[ab], (uint32_t)((n >> 1) & 1), fail)) break;
+      tc::fence_after_sync();
+      const int row = u.row0 + (warp & 1) * 32 + lane;
+      const int kvb = (part ? u.half[1] : u.half[0]) * 4;
+      const float sg = part ? u.sgn[1] : u.sgn[0];
+      uint8_t *rt0 = u.out + (int64_t)(row >> 7) * TILE;
+      const int64_t rts = (int64_t)p.t.rt * TILE;  // next piece
+      const uint32_t src = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * NMAX);
+      for (int c = 0; c < u.N; c += 32) {
+        float v[32];
+        tc::tmem_ld32(src + (uint32_t)c, v);
+        uint8_t *hi = rt0 + (int64_t)(c / KCH) * 2 * rts;
 #pragma unroll
-      for (int g = 0; g < 4; ++g) store_split8(hi, hi + rt_stride, row & 127, kvb + g, v + 8 * g, sg);
+        for (int g = 0; g < 4; ++g) store_split8(hi, hi + rts, row & 127, kvb + g, v + 8 * g, sg);
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                      tc::smem_u32(&acc_empty[ab]))
+                                  : "memory");
+      ++n;
     }
-  } else if (threadIdx.x == 0) {
-    atomicOr(err, TNMPS_EFLAG_TIMEOUT);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, ntm);
+  if (s_fail && threadIdx.x == 0) atomicOr(err, TNMPS_EFLAG_TIMEOUT);
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, NTM);
 }
 
 template <class Prob, int NMAX>
 cudaError_t launch_step(const Prob &p, int units, uint32_t *err, cudaStream_t s,
                         uint64_t *launches) {
-  const int64_t grid = (int64_t)units * p.lv.grid_m;
-  if (grid <= 0) return cudaSuccess;
+  const int64_t items = (int64_t)units * p.lv.grid_m;
+  if (items <= 0) return cudaSuccess;
+  if (items > 0x7fffffff) return cudaErrorInvalidValue;
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n_sm <= 0)
+      n_sm = 1;
+  }
   cudaError_t e = cudaFuncSetAttribute(k_swtc<Prob, NMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Ring<NMAX>::SMEM);
   if (e != cudaSuccess) return e;
-  k_swtc<Prob, NMAX><<<(unsigned)grid, 128, Ring<NMAX>::SMEM, s>>>(p, err);
+  const int grid = (int)(items < n_sm ? items : n_sm);
+  k_swtc<Prob, NMAX><<<grid, 192, Ring<NMAX>::SMEM, s>>>(p, (int)items, err);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
