@@ -40,7 +40,8 @@ std::vector<int> bond_caps(int n, int chi) {
 
 struct Layout {
   size_t sites, site_off, dims, theta_buf, w_buf, sigma, perm, scale, discarded, theta_dev, err,
-      counters, ebuf, total;
+      counters, ebuf, tc_a, tc_b, total;
+  int64_t tc_a_stride = 0, tc_b_stride = 0;  // per-state bytes of the K2 tensor-core operands
   int64_t state_elems, tw;
   std::vector<int64_t> site_off_h;
   std::vector<int> cap;
@@ -86,6 +87,14 @@ Layout make_layout(int n, int chi, int dtype, int batch, int max_params) {
   p = al256(p + 8 * CNT_NUM);
   L.ebuf = p;
   if (dtype != TNMPS_C128) p = al256(p + 16 * (size_t)batch * chi * chi);
+  L.tc_a = L.tc_b = p;
+  if (dtype == TNMPS_C64_BF16SPLIT) {
+    L.tc_a_stride = theta_tc_a_bytes(chi);
+    L.tc_b_stride = theta_tc_b_bytes(chi);
+    p = al256(p + (size_t)batch * (size_t)L.tc_a_stride);
+    L.tc_b = p;
+    p = al256(p + (size_t)batch * (size_t)L.tc_b_stride);
+  }
   L.total = p;
   return L;
 }
@@ -413,6 +422,10 @@ tnmps_status tnmps_init(tnmps_ctx **out, int n, int chi, tnmps_dtype dtype, int 
   c->err = (uint32_t *)(c->arena + L.err);
   c->counters = (unsigned long long *)(c->arena + L.counters);
   c->ebuf = c->arena + L.ebuf;
+  c->tc_a = c->arena + L.tc_a;
+  c->tc_b = c->arena + L.tc_b;
+  c->tc_a_stride = L.tc_a_stride;
+  c->tc_b_stride = L.tc_b_stride;
   c->site_off = L.site_off_h;
   c->cap = L.cap;
   c->state_elems = L.state_elems;

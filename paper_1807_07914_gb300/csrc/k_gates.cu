@@ -382,13 +382,17 @@ cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
   cudaError_t e;
   // K2: Theta = G (C_l B_{l+1})
   cudaEvent_t ev = prof_begin(c, PC_THETA);
-  ProbTheta<R> pt{};
-  pt.v = v;
-  pt.l = l;
-  pt.out = tb;
-  pt.tw = c->tw;
-  if ((e = launch_gemm<R>(pt, Mmax, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
-    return e;
+  if (c->dtype == TNMPS_C64_BF16SPLIT) {  // tensor cores, BF16 split products
+    if ((e = launch_theta_tc(c, l)) != cudaSuccess) return e;
+  } else {
+    ProbTheta<R> pt{};
+    pt.v = v;
+    pt.l = l;
+    pt.out = tb;
+    pt.tw = c->tw;
+    if ((e = launch_gemm<R>(pt, Mmax, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
+      return e;
+  }
   {
     const int work = c->ub[l] * c->ub[l + 2];
     dim3 grid((work + 255) / 256, c->batch);

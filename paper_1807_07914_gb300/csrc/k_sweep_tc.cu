@@ -14,61 +14,25 @@
 // (L, T) are written by the previous step's epilogue directly in the operand
 // layout, so intermediate results never leave the tile format.
 //
-// Real embedding of a complex product C = A B^T: with each row of B stored as
-// (Re | Im) along K, the rows of the real A that produce Re C hold (Re A | -Im
-// A) and those that produce Im C hold (Im A | Re A). An M tile covers 64
-// complex rows: accumulator lanes 0..63 are Re C, lanes 64..127 Im C. The
-// Pauli phase (+-1, +-i) only selects which K half of the destination each
-// accumulator half lands in, and its sign.
-//
-// Split precision: every real operand value is v = hi + lo (two BF16), and
-// each product is hi*hi + hi*lo + lo*hi (three MMAs; the dropped lo*lo term
-// is of relative size 2^-16), accumulated in FP32.
-//
-// Pipeline: persistent CTAs (one per SM, 192 threads) walk the output tiles.
-// One thread streams each K step's tiles (A hi/lo, B hi/lo) into a ring of
-// shared-memory stages with bulk copies on the TMA unit, counted on the
-// stage's mbarrier; one thread issues the stage's MMAs into one of two TMEM
-// accumulators and commits them to the stage's "empty" mbarrier; four warps
-// read the other accumulator with tcgen05.ld and write the split result of
-// the previous tile meanwhile. Every wait is bounded: after a timeout the CTA
-// flags TNMPS_EFLAG_TIMEOUT, waits (bounded) for its copies and MMAs in
-// flight, frees its tensor memory and returns.
-#include "sweep_tc.h"
-#include "tc_util.cuh"
+// The GEMM machinery (operand formats, real embedding, split products, the
+// persistent warp-specialised tcgen05 pipeline) is cgemm_tc.cuh; this file
+// holds the sweep's operand conversion, its two GEMM problems with their
+// epilogues, and the term dots. The Pauli phase (+-1, +-i) only selects which
+// K half of the destination each accumulator half lands in, and its sign.
+#include "cgemm_tc.cuh"
 
 namespace {
 
+using ctc::dcdiv;
+using ctc::round32;
+using ctc::store_split8;
+using ctc::tile_off;
+using ctc::Unit;
 using swtc::KCH;
 using swtc::TILE;
 
-__device__ __forceinline__ int dcdiv(int a, int b) { return (a + b - 1) / b; }
-__device__ __forceinline__ int round32(int x) { return (x + 31) & ~31; }
-
 __device__ __forceinline__ int dim_of(const TcSweep &t, int zb, int i) {
   return t.dims[(int64_t)(t.b0 + zb) * (t.n + 1) + i];
-}
-
-// byte offset of (row r, 16-byte K vector kv) inside a tile
-__device__ __forceinline__ uint32_t tile_off(int r, int kv) {
-  return (uint32_t)((r >> 3) * 1024 + kv * 128 + (r & 7) * 16);
-}
-
-// v[0..7] * sign -> the 16-byte vector (r, kv) of the hi and the lo tile
-__device__ __forceinline__ void store_split8(uint8_t *hi, uint8_t *lo, int r, int kv,
-                                             const float *v, float sign) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    uint16_t h0, l0, h1, l1;
-    tc::bf16_split(sign * v[2 * e], h0, l0);
-    tc::bf16_split(sign * v[2 * e + 1], h1, l1);
-    h[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-    l[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-  }
-  const uint32_t o = tile_off(r, kv);
-  *reinterpret_cast<uint4 *>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4 *>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // ------------------------------------------------------------ operand prep
@@ -142,22 +106,7 @@ __global__ void __launch_bounds__(256) k_root_env(TcSweep t, const int32_t *node
   }
 }
 
-// ------------------------------------------------------------ the GEMM
-// Addresses of one CTA's operands. K step kt = sh * kc + q reads
-//   A: a + sh * a_s + q * a_kt + piece * a_pc   (one 16 KB tile)
-//   B: b + sh * b_s + q * b_kt + piece * b_pc   (b_bytes = N rows x 128 B)
-struct Unit {
-  const uint8_t *a, *b;
-  int64_t a_kt, a_pc, a_s, b_kt, b_pc, b_s;
-  int kc, nk, N;
-  uint32_t b_bytes;
-  uint8_t *out;  // destination row-K matrix
-  int row0;      // destination row of accumulator row 0 of the tile
-  int half[2];   // K half of the destination for the Re / Im accumulator rows
-  float sgn[2];
-  unsigned long long flops;  // algorithmic flops to count for this item (0: none)
-};
-
+// ------------------------------------------------------------ the GEMM problems
 struct LevelArgsTc {
   const int32_t *site, *parent, *pauli;
   int nodes, grid_m;
@@ -165,11 +114,39 @@ struct LevelArgsTc {
   unsigned long long *counters;
 };
 
+// Epilogue shared by both steps: the accumulator row of this thread (Re or
+// Im part of one complex row) goes to its K half of the destination row-K
+// matrix as split BF16, 32 columns = one K chunk at a time.
+__device__ __forceinline__ void rowk_epi(const Unit &u, int warp, int lane, int c,
+                                         const float (&v)[32], int rt) {
+  const int part = warp >> 1;
+  const int row = u.row0 + (warp & 1) * 32 + lane;
+  const int kvb = (part ? u.half[1] : u.half[0]) * 4;
+  const float sg = part ? u.sgn[1] : u.sgn[0];
+  const int64_t rts = (int64_t)rt * TILE;  // next piece
+  uint8_t *hi = u.out + (int64_t)(row >> 7) * TILE + (int64_t)(c / KCH) * 2 * rts;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) store_split8(hi, hi + rts, row & 127, kvb + g, v + 8 * g, sg);
+}
+
+__device__ __forceinline__ void count_update(const Unit &u, unsigned long long *counters) {
+  if (u.flops) {
+    atomicAdd(&counters[CNT_ENV_UPDATES], 1ull);
+    atomicAdd(&counters[CNT_ENV_FLOPS], u.flops);
+  }
+}
+
 // step 1: T = (P X) contracted with the parent environment; M tile g covers
 // s' = g / MT, columns j of tile g % MT.
 struct Step1 {
   TcSweep t;
   LevelArgsTc lv;
+  static constexpr int PIECES = 2, EPI_SMEM = 0;
+  __device__ void epi(const Unit &u, int warp, int lane, int c, const float (&v)[32],
+                      uint8_t *) const {
+    rowk_epi(u, warp, lane, c, v, t.rt);
+  }
+  __device__ void done(const Unit &u) const { count_update(u, lv.counters); }
   __device__ bool setup(int item, Unit &u) const {
     const int unit = item / lv.grid_m, g = item - unit * lv.grid_m;
     const int zb = unit / lv.nodes, node = unit - zb * lv.nodes;
@@ -214,6 +191,12 @@ struct Step1 {
 struct Step2 {
   TcSweep t;
   LevelArgsTc lv;
+  static constexpr int PIECES = 2, EPI_SMEM = 0;
+  __device__ void epi(const Unit &u, int warp, int lane, int c, const float (&v)[32],
+                      uint8_t *) const {
+    rowk_epi(u, warp, lane, c, v, t.rt);
+  }
+  __device__ void done(const Unit &u) const { count_update(u, lv.counters); }
   __device__ bool setup(int item, Unit &u) const {
     const int unit = item / lv.grid_m, g = item - unit * lv.grid_m;
     const int zb = unit / lv.nodes, node = unit - zb * lv.nodes;
@@ -248,205 +231,6 @@ struct Step2 {
     return true;
   }
 };
-
-template <int NMAX>
-struct Ring {
-  static constexpr int S = NMAX <= 128 ? 3 : 2;
-  static constexpr uint32_t A_PIECE = TILE;
-  static constexpr uint32_t B_PIECE = NMAX * 128;
-  static constexpr uint32_t STAGE = 2 * A_PIECE + 2 * B_PIECE;
-  static constexpr int SMEM = 1024 + S * STAGE;
-};
-
-// Wait on an mbarrier phase unless another role of the CTA has failed; a
-// timeout marks the CTA failed. Returns true when the phase completed.
-__device__ __forceinline__ bool wait_or_fail(uint64_t *bar, uint32_t parity,
-                                             volatile int *fail) {
-  const long long t0 = clock64();
-  while (!tc::mbar_try_wait(bar, parity)) {
-    if (*fail) return false;
-    if (clock64() - t0 > 2000000000ll) {
-      *fail = 1;
-      return false;
-    }
-  }
-  return true;
-}
-
-// Persistent CTAs (one per SM) walk the items (node-state, M tile)
-// blockIdx.x, blockIdx.x + gridDim.x, ... with three roles:
-//   warp 4 (one thread): bulk copies of every K step of every item into the
-//     stage ring (a stage is refilled once the MMAs that read it completed);
-//   warp 5 (one thread): the MMAs of item i into accumulator i % 2, after the
-//     epilogue has drained that accumulator (item i - 2);
-//   warps 0-3: the epilogue of item i (warp w reads TMEM lanes 32w..32w+31),
-//     overlapping the MMAs of item i + 1.
-template <class Prob, int NMAX>
-__global__ void __launch_bounds__(192, 1) k_swtc(Prob p, int items, uint32_t *err) {
-  using RG = Ring<NMAX>;
-  constexpr int S = RG::S;
-  extern __shared__ uint8_t smraw[];
-  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
-                                            ~(uintptr_t)1023);
-  __shared__ uint64_t full[S], empty[S], acc_full[2], acc_empty[2], mma_done;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr uint32_t NTM = 2 * NMAX;  // two accumulators
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, NTM);
-    tc::tmem_relinquish();
-  }
-  if (threadIdx.x == 32) {
-    for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], 4);
-    }
-    tc::mbar_init(&mma_done, 1);
-    tc::mbar_fence_init();
-    s_fail = 0;
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tmem_base;
-  volatile int *fail = &s_fail;
-
-  if (warp == 4) {
-    if (lane == 0) {  // producer
-      int kg = 0;     // K steps issued so far (all items)
-      for (int it = blockIdx.x; it < items && !*fail; it += gridDim.x) {
-        Unit u;
-        if (!p.setup(it, u)) continue;
-        for (int kt = 0; kt < u.nk; ++kt, ++kg) {
-          const int s = kg % S;
-          if (kg >= S && !wait_or_fail(&empty[s], (uint32_t)(((kg / S) - 1) & 1), fail)) break;
-          const int sh = kt / u.kc, q = kt - sh * u.kc;
-          const uint8_t *a = u.a + sh * u.a_s + q * u.a_kt;
-          const uint8_t *b = u.b + sh * u.b_s + q * u.b_kt;
-          uint8_t *st = sm + s * RG::STAGE;
-          tc::mbar_arrive_expect_tx(&full[s], 2 * RG::A_PIECE + 2 * u.b_bytes);
-          tc::bulk_g2s(st, a, RG::A_PIECE, &full[s]);
-          tc::bulk_g2s(st + RG::A_PIECE, a + u.a_pc, RG::A_PIECE, &full[s]);
-          tc::bulk_g2s(st + 2 * RG::A_PIECE, b, u.b_bytes, &full[s]);
-          tc::bulk_g2s(st + 2 * RG::A_PIECE + RG::B_PIECE, b + u.b_pc, u.b_bytes, &full[s]);
-        }
-      }
-      // every copy issued must have landed before the CTA may leave
-      for (int k = kg > S ? kg - S : 0; k < kg; ++k)
-        if (!tc::mbar_wait(&full[k % S], (uint32_t)((k / S) & 1))) s_fail = 1;
-    }
-    __syncwarp();
-  } else if (warp == 5) {
-    if (lane == 0) {  // MMA issuer
-      int kg = 0, n = 0;  // K steps consumed, items started
-      for (int it = blockIdx.x; it < items && !*fail; it += gridDim.x) {
-        Unit u;
-        if (!p.setup(it, u)) continue;
-        const int ab = n & 1;
-        if (n >= 2 && !wait_or_fail(&acc_empty[ab], (uint32_t)(((n >> 1) - 1) & 1), fail)) break;
-        tc::fence_after_sync();
-        const uint32_t d = tmem + (uint32_t)(ab * NMAX);
-        const uint32_t idesc = tc::idesc_bf16(128, u.N);
-        bool ok = true;
-        for (int kt = 0; kt < u.nk; ++kt, ++kg) {
-          const int s = kg % S;
-          if (!wait_or_fail(&full[s], (uint32_t)((kg / S) & 1), fail)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after_sync();
-          const uint32_t a = tc::smem_u32(sm + s * RG::STAGE);
-          const uint32_t al = a + RG::A_PIECE, b = a + 2 * RG::A_PIECE, bl = b + RG::B_PIECE;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint64_t ah = tc::smem_desc(a + j * 256, 128, 1024);
-            const uint64_t alo = tc::smem_desc(al + j * 256, 128, 1024);
-            const uint64_t bh = tc::smem_desc(b + j * 256, 128, 1024);
-            const uint64_t blo = tc::smem_desc(bl + j * 256, 128, 1024);
-            tc::mma_bf16(d, ah, bh, idesc, (kt > 0 || j > 0) ? 1u : 0u);
-            tc::mma_bf16(d, ah, blo, idesc, 1u);
-            tc::mma_bf16(d, alo, bh, idesc, 1u);
-          }
-          tc::mma_commit(&empty[s]);
-        }
-        if (!ok) break;
-        tc::mma_commit(&acc_full[ab]);
-        if (u.flops) {
-          atomicAdd(&p.lv.counters[CNT_ENV_UPDATES], 1ull);
-          atomicAdd(&p.lv.counters[CNT_ENV_FLOPS], u.flops);
-        }
-        ++n;
-      }
-      // every MMA issued must have completed before the tensor memory is freed
-      tc::mma_commit(&mma_done);
-      if (!tc::mbar_wait(&mma_done, 0)) s_fail = 1;
-    }
-    __syncwarp();
-  } else {  // epilogue warps 0-3
-    const int part = warp >> 1;
-    int n = 0;
-    for (int it = blockIdx.x; it < items && !*fail; it += gridDim.x) {
-      Unit u;
-      if (!p.setup(it, u)) continue;
-      const int ab = n & 1;
-      if (!wait_or_fail(&acc_full[ab], (uint32_t)((n >> 1) & 1), fail)) break;
-      tc::fence_after_sync();
-      const int row = u.row0 + (warp & 1) * 32 + lane;
-      const int kvb = (part ? u.half[1] : u.half[0]) * 4;
-      const float sg = part ? u.sgn[1] : u.sgn[0];
-      uint8_t *rt0 = u.out + (int64_t)(row >> 7) * TILE;
-      const int64_t rts = (int64_t)p.t.rt * TILE;  // next piece
-      const uint32_t src = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * NMAX);
-      for (int c = 0; c < u.N; c += 32) {
-        float v[32];
-        tc::tmem_ld32(src + (uint32_t)c, v);
-        uint8_t *hi = rt0 + (int64_t)(c / KCH) * 2 * rts;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) store_split8(hi, hi + rts, row & 127, kvb + g, v + 8 * g, sg);
-      }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
-                                      tc::smem_u32(&acc_empty[ab]))
-                                  : "memory");
-      ++n;
-    }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (s_fail && threadIdx.x == 0) atomicOr(err, TNMPS_EFLAG_TIMEOUT);
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, NTM);
-}
-
-template <class Prob, int NMAX>
-cudaError_t launch_step(const Prob &p, int units, uint32_t *err, cudaStream_t s,
-                        uint64_t *launches) {
-  const int64_t items = (int64_t)units * p.lv.grid_m;
-  if (items <= 0) return cudaSuccess;
-  if (items > 0x7fffffff) return cudaErrorInvalidValue;
-  static int n_sm = 0;
-  if (n_sm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        n_sm <= 0)
-      n_sm = 1;
-  }
-  cudaError_t e = cudaFuncSetAttribute(k_swtc<Prob, NMAX>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Ring<NMAX>::SMEM);
-  if (e != cudaSuccess) return e;
-  const int grid = (int)(items < n_sm ? items : n_sm);
-  k_swtc<Prob, NMAX><<<grid, 192, Ring<NMAX>::SMEM, s>>>(p, (int)items, err);
-  if (launches) ++*launches;
-  return cudaGetLastError();
-}
 
 // <P_t> = Re sum_{c,c'} L[c][c'] R[c][c'], L from the split row-K environment
 __global__ void __launch_bounds__(256) k_term_dot_tc(TcSweep t, const cx<float> *renv,
@@ -515,13 +299,14 @@ cudaError_t tc_level(const TcSweep &t, const int32_t *node_site, const int32_t *
   const int units = nodes * t.nb;
   cudaError_t e;
   Step1 p1{t, lv};
-  e = t.nmax <= 128 ? launch_step<Step1, 128>(p1, units, t.err, s, launches)
-                    : launch_step<Step1, 256>(p1, units, t.err, s, launches);
+  e = t.nmax <= 128 ? ctc::launch_cgemm<Step1, 128>(p1, (int64_t)units * lv.grid_m, t.err, s, launches)
+                    : ctc::launch_cgemm<Step1, 256>(p1, (int64_t)units * lv.grid_m, t.err, s, launches);
   if (e != cudaSuccess) return e;
   lv.grid_m = mt;
   Step2 p2{t, lv};
-  return t.nmax <= 128 ? launch_step<Step2, 128>(p2, units, t.err, s, launches)
-                       : launch_step<Step2, 256>(p2, units, t.err, s, launches);
+  return t.nmax <= 128
+             ? ctc::launch_cgemm<Step2, 128>(p2, (int64_t)units * lv.grid_m, t.err, s, launches)
+             : ctc::launch_cgemm<Step2, 256>(p2, (int64_t)units * lv.grid_m, t.err, s, launches);
 }
 
 cudaError_t tc_term_dot(const TcSweep &t, const void *renv, const int64_t *roff,

@@ -139,6 +139,9 @@ struct tnmps_ctx {
   uint32_t *err = nullptr;     // device flags
   unsigned long long *counters = nullptr;  // [CNT_NUM]
   void *ebuf = nullptr;        // [batch][chi^2] complex128 Gram (complex64 form)
+  void *tc_a = nullptr;        // BF16-split form: [batch] converted K2 operands (C_l)
+  void *tc_b = nullptr;        //                  [batch] converted K2 operands (B_{l+1}^T)
+  int64_t tc_a_stride = 0, tc_b_stride = 0;
 
   // instrumentation: host-side launch count and optional per-class event timing
   uint64_t launches = 0;
@@ -214,6 +217,11 @@ cudaError_t launch_gate2(tnmps_ctx *c, const Op2 &op, const double *theta, int64
 cudaError_t launch_gate1(tnmps_ctx *c, const Op1 &op, const double *theta, int64_t th_stride);
 cudaError_t launch_move_right(tnmps_ctx *c, int site);
 cudaError_t launch_move_left(tnmps_ctx *c, int site);
+// K2 of the BF16-split form: Theta = C_l B_{l+1} on the tensor cores into
+// theta_buf (row-major, 2D_{l-1} x 2D_{l+1}); bytes per state of its operands
+cudaError_t launch_theta_tc(tnmps_ctx *c, int l);
+int64_t theta_tc_a_bytes(int chi);
+int64_t theta_tc_b_bytes(int chi);
 cudaError_t launch_jacobi_standalone(tnmps_dtype dt, int batch, int m, int n, void *a, int lda,
                                      double *sigma, int32_t *sweeps, int max_sweeps,
                                      cudaStream_t s);
