@@ -176,10 +176,33 @@ def blas_threads():
 
 def cpu_baseline(wl):
     dt, states, T, gates = oracle_sample(wl, 1)
-    return {"value": states * T / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "gates_per_s": gates / dt,
-            "sample": f"FP64 oracle (numpy/LAPACK) on 1 of the theta rows: full 390-gate "
-                      f"circuit + {T} per-term sweeps, {dt:.1f} s"}
+    out = {"value": states * T / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+           "gates_per_s": gates / dt,
+           "sample": f"FP64 oracle (numpy/LAPACK) on 1 of the theta rows: full 390-gate "
+                     f"circuit + {T} per-term sweeps, {dt:.1f} s"}
+    one = cpu_baseline_one_thread()
+    if one is not None:
+        out["one_thread"] = one
+    return out
+
+
+def cpu_baseline_one_thread():
+    """The same oracle sample with one BLAS thread: the reference arm run in a
+    child process whose thread pools are limited by the environment."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference",
+                            "--steps", "1", "--warmup", "0"], env=env, capture_output=True,
+                           text=True, timeout=600)
+        line = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": line["value"], "unit": line["unit"], "cores": 1,
+                "ms_per_sample": line["ms_per_step"]}
+    except (OSError, ValueError, IndexError, KeyError, subprocess.SubprocessError):
+        return None
 
 
 def run_reference(args):
