@@ -28,6 +28,9 @@ Network Simulations", arXiv:1807.07914):
                      value, plus the parameter-shift gradient.
 * ``mlp``         -- FP64 reference of the small MLP surrogate (forward,
                      backward, Adam) that checks the GPU training kernels.
+* ``sampling``    -- exact shot sampling of a measurement of every qubit (the
+                     MEASURE instructions of the Sec. V.B kernels), from the
+                     state vector and from the MPS, driven by input uniforms.
 
 Parity status of each function is stated in its docstring; every function
 here is pinned by a ``-m "not gpu"`` test against a closed form, a textbook
