@@ -189,6 +189,24 @@ tnmps_status tnmps_expect_pauli_sum_dev(tnmps_ctx *ctx, const tnmps_terms *terms
                                         size_t ws_bytes, double *energy_dev,
                                         double *per_term_dev);
 
+/* ---- measurement ----------------------------------------------------------
+ * Shots of a computational-basis measurement of every qubit (the MEASURE
+ * instructions that end the kernels of Sec. V.B), sampled exactly: qubits
+ * n-1, n-2, ..., 0 in turn, each drawn from its probability conditioned on
+ * the outcomes already drawn for the qubits above it.
+ *   uniforms_dev: device FP64 [batch][shots][n_qubits], values in [0, 1),
+ *     caller-owned, read during the call's GPU work. uniforms[b][k][q]
+ *     decides qubit q of shot k of state b: outcome 0 iff it is below
+ *     P(q = 0 | outcomes above q) (computed in FP64 from the state's
+ *     arithmetic type).
+ *   bits_dev: device uint8 [batch][shots][n_qubits], written 0 or 1.
+ * Moves the orthogonality centre to site n-1, as the energy calls do;
+ * allocates nothing; asynchronous on the context's stream.
+ * Errors: TNMPS_ERR_ARG (null pointer, shots < 1); a zero-norm state raises
+ * TNMPS_ERR_NUMERIC at the next synchronising call. */
+tnmps_status tnmps_sample_dev(tnmps_ctx *ctx, const double *uniforms_dev, int shots,
+                              uint8_t *bits_dev);
+
 /* ---- inspection ------------------------------------------------------------ */
 /* Synchronise and report device-side error flags. */
 tnmps_status tnmps_check(tnmps_ctx *ctx);

@@ -679,6 +679,18 @@ tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *c, const tnmps_terms *t,
   return expect_noalloc_impl(c, t->plan, t->gen, energy_dev, per_term_dev);
 }
 
+tnmps_status tnmps_sample_dev(tnmps_ctx *c, const double *uniforms_dev, int shots,
+                              uint8_t *bits_dev) {
+  if (!c) return TNMPS_ERR_ARG;
+  if (!uniforms_dev || !bits_dev) return fail(c, TNMPS_ERR_ARG, "null pointer");
+  if (shots < 1) return fail(c, TNMPS_ERR_ARG, "shots < 1");
+  tnmps_status st = inject(c);
+  if (st != TNMPS_OK) return st;
+  if ((st = move_centre(c, c->n - 1)) != TNMPS_OK) return st;
+  cudaError_t e = launch_sample(c, uniforms_dev, shots, bits_dev);
+  return e == cudaSuccess ? TNMPS_OK : cuda_fail(c, e, "sample");
+}
+
 tnmps_status tnmps_check(tnmps_ctx *c) {
   if (!c) return TNMPS_ERR_ARG;
   return sync_check(c);

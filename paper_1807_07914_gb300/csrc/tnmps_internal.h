@@ -217,6 +217,8 @@ cudaError_t launch_gate2(tnmps_ctx *c, const Op2 &op, const double *theta, int64
 cudaError_t launch_gate1(tnmps_ctx *c, const Op1 &op, const double *theta, int64_t th_stride);
 cudaError_t launch_move_right(tnmps_ctx *c, int site);
 cudaError_t launch_move_left(tnmps_ctx *c, int site);
+// Measurement shots (centre on site n-1): u [batch][shots][n] -> bits
+cudaError_t launch_sample(tnmps_ctx *c, const double *u, int shots, uint8_t *bits);
 // K2 of the BF16-split form: Theta = C_l B_{l+1} on the tensor cores into
 // theta_buf (row-major, 2D_{l-1} x 2D_{l+1}); bytes per state of its operands
 cudaError_t launch_theta_tc(tnmps_ctx *c, int l);

@@ -91,6 +91,7 @@ def lib():
         "tnmps_jacobi_svd_dev": (I, [I, I, I, I, P, I, P, P, I, P]),
         "tnmps_debug_inject": (I, [P, I, I]),
         "tnmps_expect_pauli_sum_noalloc": (I, [P, P, P, P]),
+        "tnmps_sample_dev": (I, [P, P, I, P]),
         "tnmps_gemm_bf16_dev": (I, [I, I, I, P, I, P, I, P, I, P]),
         "tnmps_mlp_bytes": (S, [I, I, I]),
         "tnmps_mlp_num_params": (C.c_int64, [I, I]),
@@ -289,6 +290,27 @@ class MPSBatch:
         the library's own static scratch replaces the workspace (asynchronous)."""
         self._check(lib().tnmps_expect_pauli_sum_noalloc(self._h, terms._h, _ptr(energy),
                                                          _ptr(per_term)))
+
+    # -------------------------------------------------------------- measurement
+    def sample_dev(self, uniforms_dev, bits_dev):
+        """Asynchronous: uniforms_dev float64 CUDA tensor [batch, shots, n] in
+        [0, 1); bits_dev uint8 CUDA tensor of the same shape receives the
+        outcomes (qubit q of shot k is 0 iff u[b, k, q] < P(0 | qubits above))."""
+        assert uniforms_dev.is_cuda and uniforms_dev.dtype == torch.float64
+        assert bits_dev.is_cuda and bits_dev.dtype == torch.uint8
+        assert uniforms_dev.shape == (self.batch, uniforms_dev.shape[1], self.n)
+        assert bits_dev.shape == uniforms_dev.shape
+        self._check(lib().tnmps_sample_dev(self._h, _ptr(uniforms_dev), uniforms_dev.shape[1],
+                                           _ptr(bits_dev)))
+
+    def sample(self, uniforms):
+        """Measurement shots as a uint8 numpy array [batch, shots, n] for
+        host uniforms [batch, shots, n] (synchronous)."""
+        u = torch.as_tensor(np.ascontiguousarray(uniforms, dtype=np.float64)).to(self.device)
+        bits = torch.empty(u.shape, dtype=torch.uint8, device=self.device)
+        self.sample_dev(u, bits)
+        self.check()
+        return bits.cpu().numpy()
 
     # -------------------------------------------------------------- inspection
     def check(self):

@@ -2,6 +2,7 @@
 
   python -m paper_1807_07914_gb300.workloads large100 [--dtype c64_bf16split] [--oracle]
   python -m paper_1807_07914_gb300.workloads rounds [--circuits 10] [--eps 1e-4] [--chi 64]
+  python -m paper_1807_07914_gb300.workloads sample [--shots 1024] [--batch 304]
 
 ``large100``: the 100-qubit single state (6 Ry/Rz + CNOT-ladder layers, 1200
 parameters, chi_max 256, cutoff 1e-8) and its 5000 random strings of weight
@@ -15,6 +16,9 @@ steps of 2, ``--circuits`` circuits each, at the paper's default cutoff 1e-4
 and a bond cap of ``--chi``: the largest bond dimension, the MPS storage in
 bytes (the paper's memory metric) and two-qubit gates per second (one circuit
 per launch sequence, so small registers are launch-latency bound).
+
+``sample``: measurement shots of all 40 qubits from the chi=128 benchmark
+states (10 ansatz layers), ``--shots`` per state: shots per second.
 """
 import argparse
 import json
@@ -108,16 +112,43 @@ def rounds(a):
                                   f"cutoff {a.eps}, chi cap {a.chi}, {a.dtype}", "rows": res}))
 
 
+def sample(a):
+    wl = inputs.workload("chi128")
+    B, T = a.batch, a.shots
+    th = torch.tensor(inputs.thetas(B, wl["n_params"], inputs.rng_for(5, 7)), dtype=torch.float64,
+                      device="cuda")
+    m = tnmps.MPSBatch(40, 128, B, dtype=a.dtype, max_params=wl["n_params"], eps=wl["eps"])
+    m.apply_circuit_dev(tnmps.gate_array(wl["circuit"]), th)
+    u = torch.rand((B, T, 40), dtype=torch.float64, device="cuda",
+                   generator=torch.Generator(device="cuda").manual_seed(1))
+    bits = torch.empty((B, T, 40), dtype=torch.uint8, device="cuda")
+    m.sample_dev(u, bits)  # warm-up (also moves the centre to the last site)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    m.sample_dev(u, bits)
+    e1.record()
+    torch.cuda.synchronize()
+    m.check()
+    t = e0.elapsed_time(e1) / 1e3
+    print(json.dumps({"workload": f"{B} chi=128 states (40 qubits, 10 layers), {T} shots each, "
+                                  "all 40 qubits measured", "dtype": a.dtype, "seconds": t,
+                      "shots_per_s": B * T / t, "max_bond": int(m.bond_dims().max()),
+                      "mean_ones": float(bits.float().mean())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("large100", "rounds"))
+    ap.add_argument("case", choices=("large100", "rounds", "sample"))
+    ap.add_argument("--shots", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--dtype", default="c64_bf16split", choices=tuple(ESIZE))
     ap.add_argument("--oracle", action="store_true")
     ap.add_argument("--circuits", type=int, default=10)
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--chi", type=int, default=64)
     a = ap.parse_args()
-    (large100 if a.case == "large100" else rounds)(a)
+    {"large100": large100, "rounds": rounds, "sample": sample}[a.case](a)
 
 
 if __name__ == "__main__":
