@@ -242,12 +242,103 @@ __device__ int within_block(cx<R> *S, int nc, int M, int Mp, R tol2, R tiny, int
   return rot;
 }
 
-// all cross pairs between two staged blocks (cyclic shifts)
-template <typename R, int E, int BC>
+// Two pairs whose x columns stay in the warp's registers (xv, in and out);
+// only the y columns move through shared memory. valid[p] = false skips
+// pair p. Returns a bitmask of the pairs rotated.
+template <typename R, int E>
+__device__ __forceinline__ int rotate_xreg2(cx<R> (&xv)[2][E], cx<R> *const *ys, const bool *valid,
+                                            int M, int lane, R tol2, R tiny) {
+  cx<R> yv[2][E];
+  R acc[8];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (valid[p]) load_col<R, E>(ys[p], M, lane, yv[p]);
+    else
+#pragma unroll
+      for (int e = 0; e < E; ++e) yv[p][e] = mkc<R>(0, 0);
+    R a = 0, bb = 0, gr = 0, gi = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      a = fma(xv[p][e].re, xv[p][e].re, fma(xv[p][e].im, xv[p][e].im, a));
+      bb = fma(yv[p][e].re, yv[p][e].re, fma(yv[p][e].im, yv[p][e].im, bb));
+      gr = fma(xv[p][e].re, yv[p][e].re, fma(xv[p][e].im, yv[p][e].im, gr));
+      gi = fma(xv[p][e].re, yv[p][e].im, fma(-xv[p][e].im, yv[p][e].re, gi));
+    }
+    acc[4 * p] = a;
+    acc[4 * p + 1] = bb;
+    acc[4 * p + 2] = gr;
+    acc[4 * p + 3] = gi;
+  }
+  warp_reduce_all<R, 8>(acc, lane);
+  int rotated = 0;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const R a = acc[4 * p], bb = acc[4 * p + 1], gr = acc[4 * p + 2], gi = acc[4 * p + 3];
+    if (!valid[p] || !(a > tiny && bb > tiny)) continue;
+    const R g2 = gr * gr + gi * gi;
+    if (!(g2 > tol2 * a * bb)) continue;
+    const R ig = frsqrt(g2);
+    const R zeta = (bb - a) * (R(0.5) * ig);
+    const R t = copysign(R(1), zeta) * frcp(fabs(zeta) + (R(1) + zeta * zeta) * frsqrt(R(1) + zeta * zeta));
+    const R c = frsqrt(R(1) + t * t);
+    const R s = c * t;
+    const R er = gr * ig, ei = -gi * ig;
+    const R ser = s * er, sei = s * ei, cer = c * er, cei = c * ei;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const cx<R> x = xv[p][e], y = yv[p][e];
+      xv[p][e] = mkc<R>(fma(c, x.re, fma(-ser, y.re, sei * y.im)),
+                        fma(c, x.im, fma(-ser, y.im, -sei * y.re)));
+      yv[p][e] = mkc<R>(fma(s, x.re, fma(cer, y.re, -cei * y.im)),
+                        fma(s, x.im, fma(cer, y.im, cei * y.re)));
+    }
+    store_col<R, E>(ys[p], M, lane, yv[p]);
+    rotated |= 1 << p;
+  }
+  return rotated;
+}
+
+// all cross pairs between two staged blocks (cyclic shifts). XREG (a CTA of
+// BC / 2 warps, two pairs per warp): warp w owns S0 columns w and w + BC/2
+// for all rounds and keeps them in registers, so only the S1 columns move
+// through shared memory.
+template <typename R, int E, int BC, bool XREG = false>
 __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp, R tol2, R tiny,
                             int &checked) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int rot = 0;
+  if constexpr (XREG) {
+    static_assert(TwoPairs<R, E>::ok, "two register-resident pairs per warp");
+    {
+      cx<R> xv[2][E];
+      const bool have[2] = {warp < n0, warp + nw < n0};
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (have[q]) load_col<R, E>(S0 + (warp + q * nw) * Mp, M, lane, xv[q]);
+        else
+#pragma unroll
+          for (int e = 0; e < E; ++e) xv[q][e] = mkc<R>(0, 0);
+      for (int t = 0; t < BC; ++t) {
+        cx<R> *ys[2];
+        bool valid[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int j = (warp + q * nw + t) % BC;
+          valid[q] = have[q] && j < n1;
+          ys[q] = S1 + j * Mp;
+        }
+        checked += (int)valid[0] + (int)valid[1];
+        const int mask = rotate_xreg2<R, E>(xv, ys, valid, M, lane, tol2, tiny);
+        rot += (mask & 1) + (mask >> 1);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (have[q]) store_col<R, E>(S0 + (warp + q * nw) * Mp, M, lane, xv[q]);
+      __syncthreads();
+      return rot;
+    }
+  } else {
   for (int t = 0; t < BC; ++t) {
     for (int k0 = warp; k0 < BC; k0 += 2 * nw) {
       cx<R> *xs[2], *ys[2];
@@ -269,6 +360,7 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
     __syncthreads();
   }
   return rot;
+  }
 }
 
 
@@ -276,8 +368,9 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
 // CTA, columns staged BC at a time in the dynamic shared memory S0/S1 (each
 // BC x 32E complex). Returns the number of sweeps run; *converged tells
 // whether the last sweep rotated nothing; *rotations / *checked count pair
-// visits (per thread: warps add their own).
-template <typename R, int BC, int E>
+// visits (per thread: warps add their own). XREG: see cross_blocks (the CTA
+// must then have BC / 2 warps).
+template <typename R, int BC, int E, bool XREG = false>
 __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, float tolfac,
                           int max_sweeps, bool *converged, int *rotations, int *checked) {
   constexpr int Mp = 32 * E;
@@ -335,7 +428,7 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
       for (int J = I + 1; J < nb; ++J) {
         ensure(1 - sI, J);
         const int nJ = min(BC, N - J * BC);
-        rot += cross_blocks<R, E, BC>(S[sI], nI, S[1 - sI], nJ, M, Mp, tol2, tiny, chk);
+        rot += cross_blocks<R, E, BC, XREG>(S[sI], nI, S[1 - sI], nJ, M, Mp, tol2, tiny, chk);
       }
     }
     if (rot && (threadIdx.x & 31) == 0) atomicAdd(&s_rot, rot);

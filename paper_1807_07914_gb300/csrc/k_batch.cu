@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
         __syncthreads();
         bool conv;
         int rot, chk;
-        jac::jacobi_run<R, BC, 8>(W, M, N, M, S0, S1, 1.0f, 30, &conv, &rot, &chk);
+        // 8 warps: with 16-column blocks each warp keeps its two x columns in registers
+        jac::jacobi_run<R, BC, 8, BC == 16>(W, M, N, M, S0, S1, 1.0f, 30, &conv, &rot, &chk);
         if (!conv && N > 1) {
           if (tid == 0) atomicOr(a.err, TNMPS_EFLAG_NOT_CONVERGED);
         }

@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(BC >= 16 ? 512 : 256) k_jacobi(JacobiArgs p) {
   cx<R> *S1 = S0 + BC * 32 * E;
   bool converged;
   int total_rot, checked;
-  const int sweep = jac::jacobi_run<R, BC, E>(W, M, N, ld, S0, S1, p.tolfac, p.max_sweeps,
-                                              &converged, &total_rot, &checked);
+  // x columns of the cross rounds in registers when the CTA has BC / 2 warps
+  constexpr bool XREG = jac::TwoPairs<R, E>::ok && (BC >= 16 ? 512 : 256) == 16 * BC;
+  const int sweep = jac::jacobi_run<R, BC, E, XREG>(W, M, N, ld, S0, S1, p.tolfac, p.max_sweeps,
+                                                    &converged, &total_rot, &checked);
   if (p.sigma_out) {  // column norms in FP64
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = warp; j < N; j += nw) {
