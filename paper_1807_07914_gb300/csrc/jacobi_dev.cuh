@@ -169,9 +169,30 @@ __device__ __forceinline__ int rotate_pairs(cx<R> *const *xs, cx<R> *const *ys, 
   return rotated;
 }
 
+// Block staging between the matrix in global memory (L2) and shared memory:
+// a warp per column, 16-byte vectors with all of a lane's loads in flight
+// together; element-wise when the column starts are not 16-byte aligned.
+template <typename R>
+__device__ __forceinline__ bool vec_ok(const cx<R> *W, int M, int ld) {
+  constexpr int V = sizeof(cx<R>) == 8 ? 2 : 1;  // complex values per 16 bytes
+  return (reinterpret_cast<uintptr_t>(W) & 15) == 0 && (M % V) == 0 && (ld % V) == 0;
+}
+
 template <typename R>
 __device__ __forceinline__ void load_block(cx<R> *__restrict__ S, const cx<R> *__restrict__ W,
                                            int col0, int ncol, int M, int ld, int Mp) {
+  if (vec_ok(W, M, ld)) {
+    constexpr int V = sizeof(cx<R>) == 8 ? 2 : 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nv = M / V;
+    for (int c = warp; c < ncol; c += nw) {
+      const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)(col0 + c) * ld);
+      float4 *dst = reinterpret_cast<float4 *>(S + c * Mp);
+#pragma unroll 4
+      for (int v = lane; v < nv; v += 32) dst[v] = src[v];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < ncol * M; e += blockDim.x) {
     const int c = e / M, r = e - c * M;
     S[c * Mp + r] = W[(int64_t)(col0 + c) * ld + r];
@@ -180,6 +201,18 @@ __device__ __forceinline__ void load_block(cx<R> *__restrict__ S, const cx<R> *_
 template <typename R>
 __device__ __forceinline__ void store_block(const cx<R> *__restrict__ S, cx<R> *__restrict__ W,
                                             int col0, int ncol, int M, int ld, int Mp) {
+  if (vec_ok(W, M, ld)) {
+    constexpr int V = sizeof(cx<R>) == 8 ? 2 : 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nv = M / V;
+    for (int c = warp; c < ncol; c += nw) {
+      const float4 *src = reinterpret_cast<const float4 *>(S + c * Mp);
+      float4 *dst = reinterpret_cast<float4 *>(W + (int64_t)(col0 + c) * ld);
+#pragma unroll 4
+      for (int v = lane; v < nv; v += 32) dst[v] = src[v];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < ncol * M; e += blockDim.x) {
     const int c = e / M, r = e - c * M;
     W[(int64_t)(col0 + c) * ld + r] = S[c * Mp + r];
