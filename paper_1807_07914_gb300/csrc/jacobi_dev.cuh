@@ -275,66 +275,96 @@ __device__ int within_block(cx<R> *S, int nc, int M, int Mp, R tol2, R tiny, int
   return rot;
 }
 
-// Two pairs whose x columns stay in the warp's registers (xv, in and out);
-// only the y columns move through shared memory. valid[p] = false skips
-// pair p. Returns a bitmask of the pairs rotated.
+// One y column (shared memory) against the warp's two register-resident x
+// columns in turn: pair A = (x1, y), then pair B = (x2, y'), y' = y after A.
+// All dot products are formed before either rotation (one warp reduction):
+// alpha1, beta, gamma1 = x1^H y, alpha2, h = x2^H y, q = x2^H x1; then
+// gamma_B = x2^H y' = s1 q + c1 e1 h and beta' = beta + t1 |gamma1| exactly.
+// valid[]: x1 / x2 / y present. Returns the number of rotations.
 template <typename R, int E>
-__device__ __forceinline__ int rotate_xreg2(cx<R> (&xv)[2][E], cx<R> *const *ys, const bool *valid,
-                                            int M, int lane, R tol2, R tiny) {
-  cx<R> yv[2][E];
-  R acc[8];
+__device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], cx<R> *ys, const bool *valid, int M,
+                                          int lane, R tol2, R tiny) {
+  cx<R> yv[E];
+  if (valid[2]) load_col<R, E>(ys, M, lane, yv);
+  else
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    if (valid[p]) load_col<R, E>(ys[p], M, lane, yv[p]);
-    else
+    for (int e = 0; e < E; ++e) yv[e] = mkc<R>(0, 0);
+  R acc[8], a2 = 0;
 #pragma unroll
-      for (int e = 0; e < E; ++e) yv[p][e] = mkc<R>(0, 0);
-    R a = 0, bb = 0, gr = 0, gi = 0;
+  for (int k = 0; k < 8; ++k) acc[k] = 0;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      a = fma(xv[p][e].re, xv[p][e].re, fma(xv[p][e].im, xv[p][e].im, a));
-      bb = fma(yv[p][e].re, yv[p][e].re, fma(yv[p][e].im, yv[p][e].im, bb));
-      gr = fma(xv[p][e].re, yv[p][e].re, fma(xv[p][e].im, yv[p][e].im, gr));
-      gi = fma(xv[p][e].re, yv[p][e].im, fma(-xv[p][e].im, yv[p][e].re, gi));
-    }
-    acc[4 * p] = a;
-    acc[4 * p + 1] = bb;
-    acc[4 * p + 2] = gr;
-    acc[4 * p + 3] = gi;
+  for (int e = 0; e < E; ++e) {
+    const cx<R> x1 = xv[0][e], x2 = xv[1][e], y = yv[e];
+    acc[0] = fma(x1.re, x1.re, fma(x1.im, x1.im, acc[0]));   // alpha1
+    acc[1] = fma(y.re, y.re, fma(y.im, y.im, acc[1]));       // beta
+    acc[2] = fma(x1.re, y.re, fma(x1.im, y.im, acc[2]));     // Re x1^H y
+    acc[3] = fma(x1.re, y.im, fma(-x1.im, y.re, acc[3]));    // Im x1^H y
+    acc[4] = fma(x2.re, y.re, fma(x2.im, y.im, acc[4]));     // Re x2^H y
+    acc[5] = fma(x2.re, y.im, fma(-x2.im, y.re, acc[5]));    // Im x2^H y
+    acc[6] = fma(x2.re, x1.re, fma(x2.im, x1.im, acc[6]));   // Re x2^H x1
+    acc[7] = fma(x2.re, x1.im, fma(-x2.im, x1.re, acc[7]));  // Im x2^H x1
+    a2 = fma(x2.re, x2.re, fma(x2.im, x2.im, a2));           // alpha2
   }
   warp_reduce_all<R, 8>(acc, lane);
+  a2 = warp_sum(a2);
   int rotated = 0;
+  R beta = acc[1], gr = acc[4], gi = acc[5];  // pair B's beta and gamma if A does not rotate
+  // pair A
+  if (valid[0] && valid[2] && acc[0] > tiny && beta > tiny) {
+    const R g1r = acc[2], g1i = acc[3], g2 = g1r * g1r + g1i * g1i;
+    if (g2 > tol2 * acc[0] * beta) {
+      const R ig = frsqrt(g2);
+      const R zeta = (beta - acc[0]) * (R(0.5) * ig);
+      const R t = copysign(R(1), zeta) * frcp(fabs(zeta) + (R(1) + zeta * zeta) * frsqrt(R(1) + zeta * zeta));
+      const R c = frsqrt(R(1) + t * t);
+      const R s = c * t;
+      const R er = g1r * ig, ei = -g1i * ig;  // e^{-i phi}
+      const R ser = s * er, sei = s * ei, cer = c * er, cei = c * ei;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    const R a = acc[4 * p], bb = acc[4 * p + 1], gr = acc[4 * p + 2], gi = acc[4 * p + 3];
-    if (!valid[p] || !(a > tiny && bb > tiny)) continue;
-    const R g2 = gr * gr + gi * gi;
-    if (!(g2 > tol2 * a * bb)) continue;
-    const R ig = frsqrt(g2);
-    const R zeta = (bb - a) * (R(0.5) * ig);
-    const R t = copysign(R(1), zeta) * frcp(fabs(zeta) + (R(1) + zeta * zeta) * frsqrt(R(1) + zeta * zeta));
-    const R c = frsqrt(R(1) + t * t);
-    const R s = c * t;
-    const R er = gr * ig, ei = -gi * ig;
-    const R ser = s * er, sei = s * ei, cer = c * er, cei = c * ei;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const cx<R> x = xv[p][e], y = yv[p][e];
-      xv[p][e] = mkc<R>(fma(c, x.re, fma(-ser, y.re, sei * y.im)),
-                        fma(c, x.im, fma(-ser, y.im, -sei * y.re)));
-      yv[p][e] = mkc<R>(fma(s, x.re, fma(cer, y.re, -cei * y.im)),
-                        fma(s, x.im, fma(cer, y.im, cei * y.re)));
+      for (int e = 0; e < E; ++e) {
+        const cx<R> x = xv[0][e], y = yv[e];
+        xv[0][e] = mkc<R>(fma(c, x.re, fma(-ser, y.re, sei * y.im)),
+                          fma(c, x.im, fma(-ser, y.im, -sei * y.re)));
+        yv[e] = mkc<R>(fma(s, x.re, fma(cer, y.re, -cei * y.im)),
+                       fma(s, x.im, fma(cer, y.im, cei * y.re)));
+      }
+      beta = beta + t * (g2 * ig);
+      // x2^H y' = s q + c e h
+      gr = fma(s, acc[6], fma(cer, acc[4], -cei * acc[5]));
+      gi = fma(s, acc[7], fma(cer, acc[5], cei * acc[4]));
+      ++rotated;
     }
-    store_col<R, E>(ys[p], M, lane, yv[p]);
-    rotated |= 1 << p;
   }
+  // pair B on y'
+  if (valid[1] && valid[2] && a2 > tiny && beta > tiny) {
+    const R g2 = gr * gr + gi * gi;
+    if (g2 > tol2 * a2 * beta) {
+      const R ig = frsqrt(g2);
+      const R zeta = (beta - a2) * (R(0.5) * ig);
+      const R t = copysign(R(1), zeta) * frcp(fabs(zeta) + (R(1) + zeta * zeta) * frsqrt(R(1) + zeta * zeta));
+      const R c = frsqrt(R(1) + t * t);
+      const R s = c * t;
+      const R er = gr * ig, ei = -gi * ig;
+      const R ser = s * er, sei = s * ei, cer = c * er, cei = c * ei;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const cx<R> x = xv[1][e], y = yv[e];
+        xv[1][e] = mkc<R>(fma(c, x.re, fma(-ser, y.re, sei * y.im)),
+                          fma(c, x.im, fma(-ser, y.im, -sei * y.re)));
+        yv[e] = mkc<R>(fma(s, x.re, fma(cer, y.re, -cei * y.im)),
+                       fma(s, x.im, fma(cer, y.im, cei * y.re)));
+      }
+      ++rotated;
+    }
+  }
+  if (rotated) store_col<R, E>(ys, M, lane, yv);
   return rotated;
 }
 
 // all cross pairs between two staged blocks (cyclic shifts). XREG (a CTA of
-// BC / 2 warps, two pairs per warp): warp w owns S0 columns w and w + BC/2
-// for all rounds and keeps them in registers, so only the S1 columns move
-// through shared memory.
+// BC / 2 warps): warp w owns S0 columns w and w + BC/2 for all rounds and
+// keeps them in registers, and each round passes one S1 column through both,
+// so only one column per two pairs moves through shared memory.
 template <typename R, int E, int BC, bool XREG = false>
 __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp, R tol2, R tiny,
                             int &checked) {
@@ -351,18 +381,13 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
         else
 #pragma unroll
           for (int e = 0; e < E; ++e) xv[q][e] = mkc<R>(0, 0);
+      // round t: warp w takes S1 column (w + t) % BC through its x columns
+      // w and w + nw in turn -- every (S0, S1) pair once over the BC rounds
       for (int t = 0; t < BC; ++t) {
-        cx<R> *ys[2];
-        bool valid[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int j = (warp + q * nw + t) % BC;
-          valid[q] = have[q] && j < n1;
-          ys[q] = S1 + j * Mp;
-        }
-        checked += (int)valid[0] + (int)valid[1];
-        const int mask = rotate_xreg2<R, E>(xv, ys, valid, M, lane, tol2, tiny);
-        rot += (mask & 1) + (mask >> 1);
+        const int j = (warp + t) % BC;
+        const bool valid[3] = {have[0], have[1], j < n1};
+        checked += valid[2] ? (int)have[0] + (int)have[1] : 0;
+        rot += rotate_x2y<R, E>(xv, S1 + j * Mp, valid, M, lane, tol2, tiny);
         __syncthreads();
       }
 #pragma unroll
