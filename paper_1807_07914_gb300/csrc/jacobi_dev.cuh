@@ -281,21 +281,31 @@ __device__ int within_block(cx<R> *S, int nc, int M, int Mp, R tol2, R tiny, int
 // alpha1, beta, gamma1 = x1^H y, alpha2, h = x2^H y, q = x2^H x1; then
 // gamma_B = x2^H y' = s1 q + c1 e1 h and beta' = beta + t1 |gamma1| exactly.
 // valid[]: x1 / x2 / y present. Returns the number of rotations.
+// ax[] carries |x1|^2, |x2|^2 through the rounds (the x columns only change
+// here): alpha - t |gamma| after a rotation, recomputed from the registers
+// when that update cancels by more than 100x.
 template <typename R, int E>
-__device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], cx<R> *ys, const bool *valid, int M,
-                                          int lane, R tol2, R tiny) {
+__device__ __forceinline__ R col_norm2(const cx<R> (&v)[E]) {
+  R q = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) q = fma(v[e].re, v[e].re, fma(v[e].im, v[e].im, q));
+  return warp_sum(q);
+}
+
+template <typename R, int E>
+__device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], R (&ax)[2], cx<R> *ys,
+                                          const bool *valid, int M, int lane, R tol2, R tiny) {
   cx<R> yv[E];
   if (valid[2]) load_col<R, E>(ys, M, lane, yv);
   else
 #pragma unroll
     for (int e = 0; e < E; ++e) yv[e] = mkc<R>(0, 0);
-  R acc[8], a2 = 0;
+  R acc[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const cx<R> x1 = xv[0][e], x2 = xv[1][e], y = yv[e];
-    acc[0] = fma(x1.re, x1.re, fma(x1.im, x1.im, acc[0]));   // alpha1
     acc[1] = fma(y.re, y.re, fma(y.im, y.im, acc[1]));       // beta
     acc[2] = fma(x1.re, y.re, fma(x1.im, y.im, acc[2]));     // Re x1^H y
     acc[3] = fma(x1.re, y.im, fma(-x1.im, y.re, acc[3]));    // Im x1^H y
@@ -303,10 +313,10 @@ __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], cx<R> *ys, const bo
     acc[5] = fma(x2.re, y.im, fma(-x2.im, y.re, acc[5]));    // Im x2^H y
     acc[6] = fma(x2.re, x1.re, fma(x2.im, x1.im, acc[6]));   // Re x2^H x1
     acc[7] = fma(x2.re, x1.im, fma(-x2.im, x1.re, acc[7]));  // Im x2^H x1
-    a2 = fma(x2.re, x2.re, fma(x2.im, x2.im, a2));           // alpha2
   }
   warp_reduce_all<R, 8>(acc, lane);
-  a2 = warp_sum(a2);
+  acc[0] = ax[0];
+  const R a2 = ax[1];
   int rotated = 0;
   R beta = acc[1], gr = acc[4], gi = acc[5];  // pair B's beta and gamma if A does not rotate
   // pair A
@@ -328,7 +338,10 @@ __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], cx<R> *ys, const bo
         yv[e] = mkc<R>(fma(s, x.re, fma(cer, y.re, -cei * y.im)),
                        fma(s, x.im, fma(cer, y.im, cei * y.re)));
       }
-      beta = beta + t * (g2 * ig);
+      const R tg = t * (g2 * ig);  // t |gamma|
+      beta = beta + tg;
+      ax[0] = acc[0] - tg;
+      if (!(ax[0] > R(0.01) * acc[0])) ax[0] = col_norm2<R, E>(xv[0]);
       // x2^H y' = s q + c e h
       gr = fma(s, acc[6], fma(cer, acc[4], -cei * acc[5]));
       gi = fma(s, acc[7], fma(cer, acc[5], cei * acc[4]));
@@ -354,6 +367,8 @@ __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], cx<R> *ys, const bo
         yv[e] = mkc<R>(fma(s, x.re, fma(cer, y.re, -cei * y.im)),
                        fma(s, x.im, fma(cer, y.im, cei * y.re)));
       }
+      ax[1] = a2 - t * (g2 * ig);
+      if (!(ax[1] > R(0.01) * a2)) ax[1] = col_norm2<R, E>(xv[1]);
       ++rotated;
     }
   }
@@ -374,20 +389,23 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
     static_assert(TwoPairs<R, E>::ok, "two register-resident pairs per warp");
     {
       cx<R> xv[2][E];
+      R ax[2];
       const bool have[2] = {warp < n0, warp + nw < n0};
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
+      for (int q = 0; q < 2; ++q) {
         if (have[q]) load_col<R, E>(S0 + (warp + q * nw) * Mp, M, lane, xv[q]);
         else
 #pragma unroll
           for (int e = 0; e < E; ++e) xv[q][e] = mkc<R>(0, 0);
+        ax[q] = col_norm2<R, E>(xv[q]);
+      }
       // round t: warp w takes S1 column (w + t) % BC through its x columns
       // w and w + nw in turn -- every (S0, S1) pair once over the BC rounds
       for (int t = 0; t < BC; ++t) {
         const int j = (warp + t) % BC;
         const bool valid[3] = {have[0], have[1], j < n1};
         checked += valid[2] ? (int)have[0] + (int)have[1] : 0;
-        rot += rotate_x2y<R, E>(xv, S1 + j * Mp, valid, M, lane, tol2, tiny);
+        rot += rotate_x2y<R, E>(xv, ax, S1 + j * Mp, valid, M, lane, tol2, tiny);
         __syncthreads();
       }
 #pragma unroll
