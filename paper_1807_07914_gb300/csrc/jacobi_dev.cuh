@@ -178,15 +178,17 @@ __device__ __forceinline__ bool vec_ok(const cx<R> *W, int M, int ld) {
   return (reinterpret_cast<uintptr_t>(W) & 15) == 0 && (M % V) == 0 && (ld % V) == 0;
 }
 
+// Block slot c holds matrix column perm[col0 + c].
 template <typename R>
 __device__ __forceinline__ void load_block(cx<R> *__restrict__ S, const cx<R> *__restrict__ W,
-                                           int col0, int ncol, int M, int ld, int Mp) {
+                                           const int *perm, int col0, int ncol, int M, int ld,
+                                           int Mp) {
   if (vec_ok(W, M, ld)) {
     constexpr int V = sizeof(cx<R>) == 8 ? 2 : 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nv = M / V;
     for (int c = warp; c < ncol; c += nw) {
-      const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)(col0 + c) * ld);
+      const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)perm[col0 + c] * ld);
       float4 *dst = reinterpret_cast<float4 *>(S + c * Mp);
 #pragma unroll 4
       for (int v = lane; v < nv; v += 32) dst[v] = src[v];
@@ -195,19 +197,20 @@ __device__ __forceinline__ void load_block(cx<R> *__restrict__ S, const cx<R> *_
   }
   for (int e = threadIdx.x; e < ncol * M; e += blockDim.x) {
     const int c = e / M, r = e - c * M;
-    S[c * Mp + r] = W[(int64_t)(col0 + c) * ld + r];
+    S[c * Mp + r] = W[(int64_t)perm[col0 + c] * ld + r];
   }
 }
 template <typename R>
 __device__ __forceinline__ void store_block(const cx<R> *__restrict__ S, cx<R> *__restrict__ W,
-                                            int col0, int ncol, int M, int ld, int Mp) {
+                                            const int *perm, int col0, int ncol, int M, int ld,
+                                            int Mp) {
   if (vec_ok(W, M, ld)) {
     constexpr int V = sizeof(cx<R>) == 8 ? 2 : 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nv = M / V;
     for (int c = warp; c < ncol; c += nw) {
       const float4 *src = reinterpret_cast<const float4 *>(S + c * Mp);
-      float4 *dst = reinterpret_cast<float4 *>(W + (int64_t)(col0 + c) * ld);
+      float4 *dst = reinterpret_cast<float4 *>(W + (int64_t)perm[col0 + c] * ld);
 #pragma unroll 4
       for (int v = lane; v < nv; v += 32) dst[v] = src[v];
     }
@@ -215,7 +218,7 @@ __device__ __forceinline__ void store_block(const cx<R> *__restrict__ S, cx<R> *
   }
   for (int e = threadIdx.x; e < ncol * M; e += blockDim.x) {
     const int c = e / M, r = e - c * M;
-    W[(int64_t)(col0 + c) * ld + r] = S[c * Mp + r];
+    W[(int64_t)perm[col0 + c] * ld + r] = S[c * Mp + r];
   }
 }
 
@@ -477,15 +480,21 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
   const R tiny = (R)((64.0 * (double)Eps<R>::u() * (double)Eps<R>::u()) * s_fro[0]);
   const int nb = (N + BC - 1) / BC;
   int held[2] = {-1, -1};
+  // column order of the sweep: the blocks are groups of BC consecutive
+  // entries of s_perm (matrix columns sorted by descending norm each sweep)
+  __shared__ int s_perm[TNMPS_JACOBI_MAX_DIM];
+  __shared__ float s_key[TNMPS_JACOBI_MAX_DIM];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) s_perm[c] = c;
+  __syncthreads();
 
   auto ensure = [&](int slot, int blk) {
     if (held[slot] == blk) return;
     if (held[slot] >= 0) {
       const int h = held[slot];
-      store_block(S[slot], W, h * BC, min(BC, N - h * BC), M, ld, Mp);
+      store_block(S[slot], W, s_perm, h * BC, min(BC, N - h * BC), M, ld, Mp);
     }
     __syncthreads();
-    load_block(S[slot], W, blk * BC, min(BC, N - blk * BC), M, ld, Mp);
+    load_block(S[slot], W, s_perm, blk * BC, min(BC, N - blk * BC), M, ld, Mp);
     held[slot] = blk;
     __syncthreads();
   };
@@ -493,6 +502,37 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
   int sweep = 0, total_rot = 0, chk = 0;
   bool conv = false;
   while (sweep < max_sweeps) {
+    // de Rijk ordering: every sweep visits the columns by descending norm
+    // (staged blocks written back first; ties keep the index order)
+    for (int s = 0; s < 2; ++s)
+      if (held[s] >= 0) {
+        store_block(S[s], W, s_perm, held[s] * BC, min(BC, N - held[s] * BC), M, ld, Mp);
+        held[s] = -1;
+      }
+    __syncthreads();
+    {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int c = warp; c < N; c += nw) {
+        float q = 0;
+        for (int r = lane; r < M; r += 32) {
+          const cx<R> z = W[(int64_t)c * ld + r];
+          q = fmaf((float)z.re, (float)z.re, fmaf((float)z.im, (float)z.im, q));
+        }
+        q = warp_sum(q);
+        if (lane == 0) s_key[c] = q;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float ki = s_key[i];
+        int rank = 0;
+        for (int j = 0; j < N; ++j) {
+          const float kj = s_key[j];
+          rank += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
+        }
+        s_perm[rank] = i;
+      }
+      __syncthreads();
+    }
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     int rot = 0;
@@ -519,7 +559,8 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
     }
   }
   for (int s = 0; s < 2; ++s)
-    if (held[s] >= 0) store_block(S[s], W, held[s] * BC, min(BC, N - held[s] * BC), M, ld, Mp);
+    if (held[s] >= 0)
+      store_block(S[s], W, s_perm, held[s] * BC, min(BC, N - held[s] * BC), M, ld, Mp);
   __syncthreads();
   *converged = conv;
   *rotations = total_rot;
