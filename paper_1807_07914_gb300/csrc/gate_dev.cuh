@@ -130,14 +130,50 @@ __device__ __forceinline__ R block_sum(R v, R *red) {
   return t;
 }
 
+// Apply (I - f v v^H)-type updates column by column: for each column x of
+// the trailing block, w = v^H x (warp reduction) and x -= coef * w * v. The
+// reflector v sits in shared memory (vs, entries j..m-1, vs[j] = 1) and a
+// warp keeps its column in registers between the dot and the update
+// (m <= 32 * HR).
+template <typename R, int HR>
+__device__ __forceinline__ void reflect_columns(cx<R> *X, int ldx, int k0, int k1, int j, int m,
+                                                const cx<R> *vs, cx<R> coef) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = k0 + warp; k < k1; k += nw) {
+    cx<R> *x = X + (int64_t)k * ldx;
+    cx<R> xr[HR];
+    cx<R> w = mkc<R>(0, 0);
+#pragma unroll
+    for (int h = 0; h < HR; ++h) {
+      const int i = j + lane + 32 * h;
+      xr[h] = i < m ? x[i] : mkc<R>(0, 0);
+      if (i < m) cfma(w, cconj(vs[i]), xr[h]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+      w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+    }
+    const cx<R> f = cmul(coef, w);
+#pragma unroll
+    for (int h = 0; h < HR; ++h) {
+      const int i = j + lane + 32 * h;
+      if (i < m) {
+        const cx<R> d = cmul(f, vs[i]);
+        x[i] = mkc<R>(xr[h].re - d.re, xr[h].im - d.im);
+      }
+    }
+  }
+}
+
 // In-place Householder QR of the column-major m x n matrix W (ld m):
 // afterwards R is the upper triangle and the reflector vectors (v_j with
 // implicit leading 1) sit below the diagonal; tau[j] holds their scalars
-// (H_j = I - tau_j v_j v_j^H, A = H_0 ... H_{r-1} R).
+// (H_j = I - tau_j v_j v_j^H, A = H_0 ... H_{r-1} R). vs: shared scratch of
+// m complex values. m <= 2 * TNMPS_MAX_CHI.
 template <typename R>
-__device__ void householder_qr(cx<R> *W, int m, int n, cx<R> *tau, R *red) {
+__device__ void householder_qr(cx<R> *W, int m, int n, cx<R> *tau, R *red, cx<R> *vs) {
   const int r = m < n ? m : n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = 0; j < r; ++j) {
     cx<R> *col = W + (int64_t)j * m;
     R part = 0;
@@ -154,43 +190,31 @@ __device__ void householder_qr(cx<R> *W, int m, int n, cx<R> *tau, R *red) {
       const R dr = alpha.re - beta, di = alpha.im;
       const R den = dr * dr + di * di;
       const cx<R> sc = mkc<R>(dr / den, -di / den);
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) col[i] = cmul(col[i], sc);
-      __syncthreads();
-      if (threadIdx.x == 0) col[j] = mkc<R>(beta, 0);
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        const cx<R> v = cmul(col[i], sc);
+        col[i] = v;
+        vs[i] = v;
+      }
+      if (threadIdx.x == 0) {
+        col[j] = mkc<R>(beta, 0);
+        vs[j] = mkc<R>(1, 0);
+      }
     }
     if (threadIdx.x == 0) tau[j] = tj;
     __syncthreads();
     if (tj.re == R(0) && tj.im == R(0)) continue;
     // columns k > j:  x <- x - conj(tau) v (v^H x)
-    const cx<R> ct = cconj(tj);
-    for (int k = j + 1 + warp; k < n; k += nw) {
-      cx<R> *x = W + (int64_t)k * m;
-      cx<R> w = mkc<R>(0, 0);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : col[i];
-        cfma(w, cconj(vi), x[i]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
-        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
-      }
-      const cx<R> f = cmul(ct, w);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : col[i];
-        const cx<R> d = cmul(f, vi);
-        x[i] = mkc<R>(x[i].re - d.re, x[i].im - d.im);
-      }
-    }
+    if (m <= 256) reflect_columns<R, 8>(W, m, j + 1, n, j, m, vs, cconj(tj));
+    else reflect_columns<R, 16>(W, m, j + 1, n, j, m, vs, cconj(tj));
     __syncthreads();
   }
 }
 
 // Q = H_0 ... H_{r-1} [I; 0] (m x r, column-major ld m) from the reflectors in W.
 template <typename R>
-__device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *tau, cx<R> *Q) {
+__device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *tau, cx<R> *Q,
+                                   cx<R> *vs) {
   const int r = m < n ? m : n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
     const int q = e / m, i = e - q * m;
     Q[e] = mkc<R>(i == q ? R(1) : R(0), 0);
@@ -200,25 +224,10 @@ __device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *ta
     const cx<R> tj = tau[j];
     if (tj.re == R(0) && tj.im == R(0)) continue;
     const cx<R> *v = W + (int64_t)j * m;
-    for (int q = j + warp; q < r; q += nw) {
-      cx<R> *x = Q + (int64_t)q * m;
-      cx<R> w = mkc<R>(0, 0);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : v[i];
-        cfma(w, cconj(vi), x[i]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
-        w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
-      }
-      const cx<R> f = cmul(tj, w);
-      for (int i = j + lane; i < m; i += 32) {
-        const cx<R> vi = (i == j) ? mkc<R>(1, 0) : v[i];
-        const cx<R> d = cmul(f, vi);
-        x[i] = mkc<R>(x[i].re - d.re, x[i].im - d.im);
-      }
-    }
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vs[i] = i == j ? mkc<R>(1, 0) : v[i];
+    __syncthreads();
+    if (m <= 256) reflect_columns<R, 8>(Q, m, j, r, j, m, vs, tj);
+    else reflect_columns<R, 16>(Q, m, j, r, j, m, vs, tj);
     __syncthreads();
   }
 }
@@ -231,6 +240,7 @@ template <typename R>
 __device__ int qr_right_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
   const int m = 2 * Dl, n = Dr, r = m < n ? m : n;
   __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
+  __shared__ cx<R> vs[2 * TNMPS_MAX_CHI];
   __shared__ R red[32];
   __syncthreads();
   for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
@@ -238,8 +248,8 @@ __device__ int qr_right_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
     W[e] = X[(int64_t)i * n + k];
   }
   __syncthreads();
-  householder_qr(W, m, n, tau, red);
-  householder_form_q(W, m, n, tau, Qbuf);
+  householder_qr(W, m, n, tau, red, vs);
+  householder_form_q(W, m, n, tau, Qbuf, vs);
   for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
     const int i = e / r, q = e - i * r;
     X[e] = Qbuf[(int64_t)q * m + i];
@@ -255,12 +265,13 @@ template <typename R>
 __device__ int lq_left_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
   const int m = 2 * Dr, n = Dl, r = m < n ? m : n;
   __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
+  __shared__ cx<R> vs[2 * TNMPS_MAX_CHI];
   __shared__ R red[32];
   __syncthreads();
   for (int e = threadIdx.x; e < m * n; e += blockDim.x) W[e] = cconj(X[e]);
   __syncthreads();
-  householder_qr(W, m, n, tau, red);
-  householder_form_q(W, m, n, tau, Qbuf);
+  householder_qr(W, m, n, tau, red, vs);
+  householder_form_q(W, m, n, tau, Qbuf, vs);
   for (int e = threadIdx.x; e < r * m; e += blockDim.x) X[e] = cconj(Qbuf[e]);
   __syncthreads();
   return r;
