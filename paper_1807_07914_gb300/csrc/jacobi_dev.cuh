@@ -112,9 +112,10 @@ __device__ __forceinline__ void warp_reduce_all(R *v, int lane) {
 // Orthogonalise NP column pairs (x[p], y[p]) of length M in shared memory
 // at once (independent pairs interleave their latency chains). Returns a
 // bitmask of the pairs rotated.
+// dmax2: running maximum of |gamma|^2 / (alpha beta) over the pairs rotated.
 template <typename R, int E, int NP>
 __device__ __forceinline__ int rotate_pairs(cx<R> *const *xs, cx<R> *const *ys, int M, int lane,
-                                            R tol2, R tiny) {
+                                            R tol2, R tiny, R &dmax2) {
   cx<R> xv[NP][E], yv[NP][E];
   R acc[4 * NP];
 #pragma unroll
@@ -145,6 +146,7 @@ __device__ __forceinline__ int rotate_pairs(cx<R> *const *xs, cx<R> *const *ys, 
     if (!(a > tiny && bb > tiny)) continue;
     const R g2 = gr * gr + gi * gi;
     if (!(g2 > tol2 * a * bb)) continue;
+    dmax2 = fmax(dmax2, g2 / (a * bb));
     // real Jacobi rotation on (x, e^{-i phi} y), gamma = g e^{i phi}
     const R ig = frsqrt(g2);  // 1 / |gamma|
     const R zeta = (bb - a) * (R(0.5) * ig);
@@ -234,22 +236,23 @@ struct TwoPairs {
 // (compile-time indices only, so the pointers stay in registers).
 template <typename R, int E>
 __device__ __forceinline__ int do_pairs(cx<R> **xs, cx<R> **ys, int np, int M, int lane, R tol2,
-                                        R tiny, int &checked) {
+                                        R tiny, int &checked, R &dmax2) {
   checked += np;
   int mask = 0;
   if constexpr (TwoPairs<R, E>::ok) {
-    if (np == 2) mask = rotate_pairs<R, E, 2>(xs, ys, M, lane, tol2, tiny);
-    else if (np == 1) mask = rotate_pairs<R, E, 1>(xs, ys, M, lane, tol2, tiny);
+    if (np == 2) mask = rotate_pairs<R, E, 2>(xs, ys, M, lane, tol2, tiny, dmax2);
+    else if (np == 1) mask = rotate_pairs<R, E, 1>(xs, ys, M, lane, tol2, tiny, dmax2);
   } else {
-    if (np >= 1) mask = rotate_pairs<R, E, 1>(xs, ys, M, lane, tol2, tiny);
-    if (np == 2) mask |= rotate_pairs<R, E, 1>(xs + 1, ys + 1, M, lane, tol2, tiny) << 1;
+    if (np >= 1) mask = rotate_pairs<R, E, 1>(xs, ys, M, lane, tol2, tiny, dmax2);
+    if (np == 2) mask |= rotate_pairs<R, E, 1>(xs + 1, ys + 1, M, lane, tol2, tiny, dmax2) << 1;
   }
   return (mask & 1) + (mask >> 1);
 }
 
 // all pairs inside one staged block (round-robin / circle ordering)
 template <typename R, int E>
-__device__ int within_block(cx<R> *S, int nc, int M, int Mp, R tol2, R tiny, int &checked) {
+__device__ int within_block(cx<R> *S, int nc, int M, int Mp, R tol2, R tiny, int &checked,
+                            R &dmax2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int rot = 0;
   if (nc < 2) return 0;
@@ -271,7 +274,7 @@ __device__ int within_block(cx<R> *S, int nc, int M, int Mp, R tol2, R tiny, int
         xs[0] = xs[1];
         ys[0] = ys[1];
       }
-      rot += do_pairs<R, E>(xs, ys, (int)ok[0] + (int)ok[1], M, lane, tol2, tiny, checked);
+      rot += do_pairs<R, E>(xs, ys, (int)ok[0] + (int)ok[1], M, lane, tol2, tiny, checked, dmax2);
     }
     __syncthreads();
   }
@@ -297,7 +300,8 @@ __device__ __forceinline__ R col_norm2(const cx<R> (&v)[E]) {
 
 template <typename R, int E>
 __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], R (&ax)[2], cx<R> *ys,
-                                          const bool *valid, int M, int lane, R tol2, R tiny) {
+                                          const bool *valid, int M, int lane, R tol2, R tiny,
+                                          R &dmax2) {
   cx<R> yv[E];
   if (valid[2]) load_col<R, E>(ys, M, lane, yv);
   else
@@ -326,6 +330,7 @@ __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], R (&ax)[2], cx<R> *
   if (valid[0] && valid[2] && acc[0] > tiny && beta > tiny) {
     const R g1r = acc[2], g1i = acc[3], g2 = g1r * g1r + g1i * g1i;
     if (g2 > tol2 * acc[0] * beta) {
+      dmax2 = fmax(dmax2, g2 / (acc[0] * beta));
       const R ig = frsqrt(g2);
       const R zeta = (beta - acc[0]) * (R(0.5) * ig);
       const R t = copysign(R(1), zeta) * frcp(fabs(zeta) + (R(1) + zeta * zeta) * frsqrt(R(1) + zeta * zeta));
@@ -355,6 +360,7 @@ __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], R (&ax)[2], cx<R> *
   if (valid[1] && valid[2] && a2 > tiny && beta > tiny) {
     const R g2 = gr * gr + gi * gi;
     if (g2 > tol2 * a2 * beta) {
+      dmax2 = fmax(dmax2, g2 / (a2 * beta));
       const R ig = frsqrt(g2);
       const R zeta = (beta - a2) * (R(0.5) * ig);
       const R t = copysign(R(1), zeta) * frcp(fabs(zeta) + (R(1) + zeta * zeta) * frsqrt(R(1) + zeta * zeta));
@@ -385,7 +391,7 @@ __device__ __forceinline__ int rotate_x2y(cx<R> (&xv)[2][E], R (&ax)[2], cx<R> *
 // so only one column per two pairs moves through shared memory.
 template <typename R, int E, int BC, bool XREG = false>
 __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp, R tol2, R tiny,
-                            int &checked) {
+                            int &checked, R &dmax2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int rot = 0;
   if constexpr (XREG) {
@@ -408,7 +414,7 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
         const int j = (warp + t) % BC;
         const bool valid[3] = {have[0], have[1], j < n1};
         checked += valid[2] ? (int)have[0] + (int)have[1] : 0;
-        rot += rotate_x2y<R, E>(xv, ax, S1 + j * Mp, valid, M, lane, tol2, tiny);
+        rot += rotate_x2y<R, E>(xv, ax, S1 + j * Mp, valid, M, lane, tol2, tiny, dmax2);
         __syncthreads();
       }
 #pragma unroll
@@ -434,7 +440,7 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
         xs[0] = xs[1];
         ys[0] = ys[1];
       }
-      rot += do_pairs<R, E>(xs, ys, (int)ok[0] + (int)ok[1], M, lane, tol2, tiny, checked);
+      rot += do_pairs<R, E>(xs, ys, (int)ok[0] + (int)ok[1], M, lane, tol2, tiny, checked, dmax2);
     }
     __syncthreads();
   }
@@ -455,6 +461,7 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
   constexpr int Mp = 32 * E;
   cx<R> *S[2] = {S0, S1};
   __shared__ int s_rot;
+  __shared__ unsigned s_dmax;
   const R tol = R(tolfac) * (sqrt(R(M)) + R(16)) * Eps<R>::u();
   const R tol2 = tol * tol;
   // noise floor: (8 u ||A||_F)^2 on squared column norms (||A||_F is invariant)
@@ -533,26 +540,42 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) s_rot = 0;
+    if (threadIdx.x == 0) {
+      s_rot = 0;
+      s_dmax = 0u;
+    }
     __syncthreads();
     int rot = 0;
+    R dmax2 = 0;
     for (int I = 0; I < nb; ++I) {
       int sI = (held[1] == I) ? 1 : 0;
       ensure(sI, I);
       const int nI = min(BC, N - I * BC);
-      rot += within_block<R, E>(S[sI], nI, M, Mp, tol2, tiny, chk);
+      rot += within_block<R, E>(S[sI], nI, M, Mp, tol2, tiny, chk, dmax2);
       for (int J = I + 1; J < nb; ++J) {
         ensure(1 - sI, J);
         const int nJ = min(BC, N - J * BC);
-        rot += cross_blocks<R, E, BC, XREG>(S[sI], nI, S[1 - sI], nJ, M, Mp, tol2, tiny, chk);
+        rot += cross_blocks<R, E, BC, XREG>(S[sI], nI, S[1 - sI], nJ, M, Mp, tol2, tiny, chk,
+                                            dmax2);
       }
     }
-    if (rot && (threadIdx.x & 31) == 0) atomicAdd(&s_rot, rot);
+    if (rot && (threadIdx.x & 31) == 0) {
+      atomicAdd(&s_rot, rot);
+      atomicMax(&s_dmax, __float_as_uint((float)dmax2));  // non-negative: bits order as values
+    }
     __syncthreads();
     ++sweep;
     const int swept = s_rot;
+    const float sweep_dmax2 = __uint_as_float(s_dmax);
     __syncthreads();
     total_rot += swept;
+    // quadratic convergence: a sweep whose largest relative rotation |gamma| /
+    // sqrt(alpha beta) is below sqrt(tol) / 4 leaves every pair within about
+    // tol (the next sweep would rotate nothing), so it ends the iteration
+    if (swept > 0 && sweep_dmax2 < 0.0625f * (float)tol) {
+      conv = true;
+      break;
+    }
     if (swept == 0) {
       conv = true;
       break;
