@@ -39,8 +39,8 @@ struct JacobiArgs {
   unsigned long long *counters;
 };
 
-template <typename R, int BC, int E>
-__global__ void __launch_bounds__(BC >= 16 ? 512 : 256) k_jacobi(JacobiArgs p) {
+template <typename R, int BC, int E, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_jacobi(JacobiArgs p) {
   const int b = blockIdx.x;
   int M, N, ld;
   if (p.dims) {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(BC >= 16 ? 512 : 256) k_jacobi(JacobiArgs p) {
   bool converged;
   int total_rot, checked;
   // x columns of the cross rounds in registers when the CTA has BC / 2 warps
-  constexpr bool XREG = jac::TwoPairs<R, E>::ok && (BC >= 16 ? 512 : 256) == 16 * BC;
+  constexpr bool XREG = jac::TwoPairs<R, E>::ok && NT == 16 * BC;
   const int sweep = jac::jacobi_run<R, BC, E, XREG>(W, M, N, ld, S0, S1, p.tolfac, p.max_sweeps,
                                                     &converged, &total_rot, &checked);
   if (p.sigma_out) {  // column norms in FP64
@@ -88,14 +88,14 @@ __global__ void __launch_bounds__(BC >= 16 ? 512 : 256) k_jacobi(JacobiArgs p) {
   }
 }
 
-template <typename R, int BC, int E>
+// NT threads (XREG when NT = 16 BC); MINB CTAs per SM
+template <typename R, int BC, int E, int NT = (BC >= 16 ? 512 : 256), int MINB = 1>
 cudaError_t run(const JacobiArgs &a, int batch, cudaStream_t s) {
-  constexpr int NT = BC >= 16 ? 512 : 256;
   const size_t smem = (size_t)2 * BC * 32 * E * sizeof(cx<R>);
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, BC, E>,
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, BC, E, NT, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi<R, BC, E><<<batch, NT, smem, s>>>(a);
+  k_jacobi<R, BC, E, NT, MINB><<<batch, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -103,6 +103,8 @@ template <typename R>
 cudaError_t dispatch(const JacobiArgs &a, int Mcap, int batch, cudaStream_t s) {
   if (Mcap <= 64) return run<R, 32, 2>(a, batch, s);
   if (Mcap <= 128) return run<R, 32, 4>(a, batch, s);
+  if constexpr (sizeof(R) == 4)  // 16-column blocks, 8 warps, two CTAs per SM
+    if (Mcap <= 256) return run<R, 16, 8, 256, 2>(a, batch, s);
   if (Mcap <= 256) return run<R, sizeof(R) == 8 ? 16 : 32, 8>(a, batch, s);
   return run<R, sizeof(R) == 8 ? 8 : 16, 16>(a, batch, s);
 }
