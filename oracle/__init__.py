@@ -31,6 +31,11 @@ Network Simulations", arXiv:1807.07914):
 * ``sampling``    -- exact shot sampling of a measurement of every qubit (the
                      MEASURE instructions of the Sec. V.B kernels), from the
                      state vector and from the MPS, driven by input uniforms.
+* ``supergate``   -- application of an aggregate of gates on any qubits by
+                     maximising the overlap of an output MPS with the input
+                     network plus the gates (Sec. II, general gate action;
+                     Sec. IV, ExaTENSOR MPS visitor): the gates as an MPO,
+                     left/right environments and two-site updates.
 
 Parity status of each function is stated in its docstring; every function
 here is pinned by a ``-m "not gpu"`` test against a closed form, a textbook
