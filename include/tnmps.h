@@ -54,6 +54,7 @@ extern "C" {
 
 typedef struct tnmps_ctx tnmps_ctx;
 typedef struct tnmps_terms tnmps_terms;
+typedef struct tnmps_supergate tnmps_supergate;
 
 /* Arithmetic of the state and of the contractions. TNMPS_C128: complex128
  * everywhere (the plain FP64 form). TNMPS_C64: complex64 storage and FP32
@@ -118,7 +119,9 @@ typedef enum {
   TNMPS_PROF_TERM = 6,    /* term values and energy reduction (K6)              */
   TNMPS_PROF_ENV_TC = 7,  /* tensor-core GEMM steps of the K5 sweeps (BF16-split
                              form; nested inside TNMPS_PROF_ENV)                */
-  TNMPS_PROF_NUM = 8
+  TNMPS_PROF_FIT = 8,     /* super-gate fit contractions: environments and the
+                             two-site gradient (its splits count as JACOBI/SPLIT) */
+  TNMPS_PROF_NUM = 9
 } tnmps_prof_class;
 
 const char *tnmps_status_string(tnmps_status s);
@@ -206,6 +209,56 @@ tnmps_status tnmps_expect_pauli_sum_dev(tnmps_ctx *ctx, const tnmps_terms *terms
  * TNMPS_ERR_NUMERIC at the next synchronising call. */
 tnmps_status tnmps_sample_dev(tnmps_ctx *ctx, const double *uniforms_dev, int shots,
                               uint8_t *bits_dev);
+
+/* ---- super-gates by overlap maximisation ----------------------------------
+ * The general gate action of Sec. II (steps 1-6) and of Sec. IV's ExaTENSOR
+ * MPS visitor: an ordered aggregate of gates on any qubits (a super-gate) is
+ * applied by optimising an output MPS TN_out so that the closed network
+ * <TN_out | gates . TN_inp> is as large as possible.
+ *
+ * tnmps_supergate_create: gates as for tnmps_apply_circuit (any distance
+ * between the qubits of a two-qubit gate), parameters bound from theta[n_params]
+ * (host, read during the call). The host builds the gates as a matrix-product
+ * operator over the window [first, last] of qubits they touch (two-qubit
+ * gates through an exact operator-Schmidt split, bonds reduced to the ranks of
+ * the operator's cuts, at most 64). TNMPS_ERR_ARG on a bad gate,
+ * TNMPS_ERR_UNSUPPORTED if an MPO bond would exceed 64. No device work. */
+tnmps_status tnmps_supergate_create(tnmps_supergate **out, int n_qubits, const tnmps_gate *gates,
+                                    size_t n_gates, const double *theta, size_t n_params);
+void tnmps_supergate_free(tnmps_supergate *sg);
+/* Window and MPO bonds: bonds[last - first + 2], bonds[0] = bonds[end] = 1
+ * (either pointer may be NULL). */
+tnmps_status tnmps_supergate_info(const tnmps_supergate *sg, int32_t *first, int32_t *last,
+                                  int32_t *bonds);
+/* The MPO tensors, site first..last in order, each [w_left][2 out][2 in]
+ * [w_right] row-major, as interleaved complex128 (cap = doubles available;
+ * TNMPS_ERR_NOMEM if too small). */
+tnmps_status tnmps_supergate_mpo(const tnmps_supergate *sg, double *out, size_t cap);
+/* Device workspace bytes of tnmps_apply_supergate for this context (0 on a
+ * mismatch of register sizes). */
+size_t tnmps_supergate_workspace_bytes(const tnmps_ctx *ctx, const tnmps_supergate *sg);
+/* Apply the super-gate to every state of the context. Stages: (3) TN_out is
+ * a copy of the state, first brought to the gates applied one by one
+ * (adjacent pairs, SWAP chains, truncation under the stage's bond cap);
+ * (5) left-to-right sweeps of two-site updates over the window, each update
+ * the normalised gradient of the overlap with respect to the two-site block,
+ * split by the SVD and the cutoff rule under the bond cap, until no state's
+ * fidelity F = |<TN_out|gates TN_inp>|^2 rises by tol in a sweep (or
+ * max_sweeps); (6) while some state has 1 - F > target and the cap is below
+ * chi_max (<= the context's chi_max), the cap (initially the largest bond of
+ * the input inside the window) doubles and the stage repeats from the copy.
+ * Sites outside the window keep the input's tensors. The discarded weight of
+ * each state grows by 1 - F.
+ *   ws: device workspace of tnmps_supergate_workspace_bytes (256-byte
+ *       aligned), caller-owned.
+ *   fidelity[batch], fidelity_start[batch] (F of the last stage's first
+ *   iterate), info[3] = {sweeps, stages, final bond cap}: host outputs, each
+ *   may be NULL. Synchronises the context's stream (one read of the
+ *   overlaps per sweep). */
+tnmps_status tnmps_apply_supergate(tnmps_ctx *ctx, const tnmps_supergate *sg, int chi_max,
+                                   double target, double tol, int max_sweeps, void *ws,
+                                   size_t ws_bytes, double *fidelity, double *fidelity_start,
+                                   int32_t *info);
 
 /* ---- inspection ------------------------------------------------------------ */
 /* Synchronise and report device-side error flags. */

@@ -20,6 +20,16 @@ struct tnmps_terms {
   uint64_t gen = 0;
 };
 
+// A super-gate: the gate list with its parameters bound, and the same gates as
+// a matrix-product operator over the window [p, q] of qubits they touch.
+struct tnmps_supergate {
+  int n = 0, p = 0, q = 0;
+  std::vector<int> w;             // MPO bonds, w[0] = w[q-p+1] = 1
+  std::vector<std::complex<double>> W;  // site tensors [w_{i-1}][2 out][2 in][w_i]
+  std::vector<int64_t> woff;      // element offset of each window site
+  std::vector<tnmps_gate> gates;  // fixed-angle copy of the gate list
+};
+
 namespace {
 
 std::atomic<uint64_t> g_plan_gen{1};
@@ -215,6 +225,211 @@ void push_fac(std::vector<Fac1> &v, const Fac1 &f) {
     return;
   }
   v.push_back(f);
+}
+
+// ------------------------------------------------------- super-gate MPO
+// Dense complex matrix, row-major.
+struct ZMat {
+  int r = 0, c = 0;
+  std::vector<zc> a;
+  ZMat() = default;
+  ZMat(int r_, int c_) : r(r_), c(c_), a((size_t)r_ * c_) {}
+  zc &at(int i, int j) { return a[(size_t)i * c + j]; }
+  zc at(int i, int j) const { return a[(size_t)i * c + j]; }
+};
+
+// X = Q C with Q (rows x k) orthonormal columns spanning X's columns and
+// C = Q^H X: Gram-Schmidt over the columns (two projection passes), a column
+// whose remainder is below tol * (largest column norm) adds nothing. k >= 1.
+void column_basis(const ZMat &X, double tol, ZMat &Q, ZMat &C) {
+  double mx = 0;
+  for (int j = 0; j < X.c; ++j) {
+    double s = 0;
+    for (int i = 0; i < X.r; ++i) s += std::norm(X.at(i, j));
+    mx = std::max(mx, sqrt(s));
+  }
+  std::vector<std::vector<zc>> basis;
+  for (int j = 0; j < X.c; ++j) {
+    std::vector<zc> v(X.r);
+    for (int i = 0; i < X.r; ++i) v[i] = X.at(i, j);
+    for (int pass = 0; pass < 2; ++pass)
+      for (const auto &b : basis) {
+        zc h = 0;
+        for (int i = 0; i < X.r; ++i) h += std::conj(b[i]) * v[i];
+        for (int i = 0; i < X.r; ++i) v[i] -= h * b[i];
+      }
+    double nv = 0;
+    for (int i = 0; i < X.r; ++i) nv += std::norm(v[i]);
+    nv = sqrt(nv);
+    if (nv > tol * mx && nv > 0) {
+      for (auto &x : v) x /= nv;
+      basis.push_back(std::move(v));
+    }
+  }
+  if (basis.empty()) {
+    basis.emplace_back(X.r, zc(0));
+    basis[0][0] = 1;
+  }
+  const int k = (int)basis.size();
+  Q = ZMat(X.r, k);
+  C = ZMat(k, X.c);
+  for (int t = 0; t < k; ++t) {
+    for (int i = 0; i < X.r; ++i) Q.at(i, t) = basis[t][i];
+    for (int j = 0; j < X.c; ++j) {
+      zc h = 0;
+      for (int i = 0; i < X.r; ++i) h += std::conj(basis[t][i]) * X.at(i, j);
+      C.at(t, j) = h;
+    }
+  }
+}
+
+// MPO site tensor T[al][o][s][be]
+struct MpoSite {
+  int wl = 1, wr = 1;
+  std::vector<zc> t;
+  zc &at(int al, int o, int s, int be) { return t[(((size_t)al * 2 + o) * 2 + s) * wr + be]; }
+};
+
+// Remove linearly dependent directions of every bond: a left-to-right pass
+// that reduces each site to an orthonormal column basis of (al o s) x be and
+// moves the coefficients into the next site, then the mirror pass from the
+// right. The operator is unchanged (up to the tolerance); the bonds become the
+// ranks of the operator's cuts.
+void compress_mpo(std::vector<MpoSite> &T) {
+  const double tol = 1e-13;
+  const int m = (int)T.size();
+  for (int i = 0; i + 1 < m; ++i) {
+    MpoSite &A = T[i], &B = T[i + 1];
+    ZMat X(A.wl * 4, A.wr), Q, C;
+    for (size_t e = 0; e < A.t.size(); ++e) X.a[e] = A.t[e];
+    column_basis(X, tol, Q, C);
+    const int k = Q.c;
+    A.wr = k;
+    A.t = Q.a;
+    MpoSite nb;
+    nb.wl = k;
+    nb.wr = B.wr;
+    nb.t.assign((size_t)k * 4 * B.wr, zc(0));
+    for (int kk = 0; kk < k; ++kk)
+      for (int be = 0; be < B.wl; ++be) {
+        const zc f = C.at(kk, be);
+        if (f == zc(0)) continue;
+        for (size_t r = 0; r < (size_t)4 * B.wr; ++r) nb.t[kk * 4 * B.wr + r] += f * B.t[be * 4 * B.wr + r];
+      }
+    B = std::move(nb);
+  }
+  for (int i = m - 1; i > 0; --i) {
+    MpoSite &A = T[i], &P = T[i - 1];
+    // Z = A^T as (o s be) x al
+    ZMat Z(4 * A.wr, A.wl), Q, C;
+    for (int al = 0; al < A.wl; ++al)
+      for (int r = 0; r < 4 * A.wr; ++r) Z.at(r, al) = A.t[(size_t)al * 4 * A.wr + r];
+    column_basis(Z, tol, Q, C);
+    const int k = Q.c;
+    MpoSite na;
+    na.wl = k;
+    na.wr = A.wr;
+    na.t.assign((size_t)k * 4 * A.wr, zc(0));
+    for (int kk = 0; kk < k; ++kk)
+      for (int r = 0; r < 4 * A.wr; ++r) na.t[(size_t)kk * 4 * A.wr + r] = Q.at(r, kk);
+    A = std::move(na);
+    // P[.., al] -> sum_al P[.., al] C[k, al]
+    MpoSite np;
+    np.wl = P.wl;
+    np.wr = k;
+    np.t.assign((size_t)P.wl * 4 * k, zc(0));
+    for (int row = 0; row < P.wl * 4; ++row)
+      for (int kk = 0; kk < k; ++kk) {
+        zc acc = 0;
+        for (int al = 0; al < P.wr; ++al) acc += P.t[(size_t)row * P.wr + al] * C.at(kk, al);
+        np.t[(size_t)row * k + kk] = acc;
+      }
+    P = std::move(np);
+  }
+}
+
+// Gate matrix of a (bound) one-qubit gate.
+void gate_1q(const tnmps_gate &g, zc U[4]) {
+  if (is_rot(g.op)) rot_1q(g.op, g.angle, U);
+  else fixed_1q(g.op, U);
+}
+
+tnmps_status build_supergate(tnmps_supergate &sg, std::string &err) {
+  const int m = sg.q - sg.p + 1;
+  std::vector<MpoSite> T(m);
+  for (auto &t : T) {
+    t.t.assign(4, zc(0));
+    t.at(0, 0, 0, 0) = 1;
+    t.at(0, 1, 1, 0) = 1;
+  }
+  for (const tnmps_gate &g : sg.gates) {
+    if (is_1q(g.op)) {
+      zc U[4];
+      gate_1q(g, U);
+      MpoSite &A = T[g.q0 - sg.p];
+      std::vector<zc> o(A.t.size());
+      for (int al = 0; al < A.wl; ++al)
+        for (int s = 0; s < 2; ++s)
+          for (int be = 0; be < A.wr; ++be)
+            for (int oo = 0; oo < 2; ++oo)
+              o[(((size_t)al * 2 + oo) * 2 + s) * A.wr + be] =
+                  U[2 * oo] * A.at(al, 0, s, be) + U[2 * oo + 1] * A.at(al, 1, s, be);
+      A.t = o;
+      continue;
+    }
+    const int qa = std::min(g.q0, g.q1), qb = std::max(g.q0, g.q1);
+    zc G[16];
+    core_2q(g.op, g.q0 == qa, G);  // basis 2 s_left + s_right
+    // M[(oa ia), (ob ib)] = G[(oa ob), (ia ib)] = sum_k A_k[(oa ia)] B_k[(ob ib)]
+    ZMat M(4, 4), Q, C;
+    for (int oa = 0; oa < 2; ++oa)
+      for (int ob = 0; ob < 2; ++ob)
+        for (int ia = 0; ia < 2; ++ia)
+          for (int ib = 0; ib < 2; ++ib)
+            M.at(2 * oa + ia, 2 * ob + ib) = G[4 * (2 * oa + ob) + 2 * ia + ib];
+    column_basis(M, 1e-13, Q, C);
+    const int r = Q.c;
+    const int i = qa - sg.p, j = qb - sg.p;
+    for (int site = i; site <= j; ++site) {
+      MpoSite &A = T[site];
+      MpoSite nA;
+      nA.wl = site == i ? A.wl : A.wl * r;
+      nA.wr = site == j ? A.wr : A.wr * r;
+      nA.t.assign((size_t)nA.wl * 4 * nA.wr, zc(0));
+      for (int k = 0; k < r; ++k)
+        for (int al = 0; al < A.wl; ++al)
+          for (int be = 0; be < A.wr; ++be)
+            for (int o = 0; o < 2; ++o)
+              for (int s = 0; s < 2; ++s) {
+                zc v;
+                if (site == i)
+                  v = Q.at(2 * o + 0, k) * A.at(al, 0, s, be) + Q.at(2 * o + 1, k) * A.at(al, 1, s, be);
+                else if (site == j)
+                  v = C.at(k, 2 * o + 0) * A.at(al, 0, s, be) + C.at(k, 2 * o + 1) * A.at(al, 1, s, be);
+                else
+                  v = A.at(al, o, s, be);
+                const int nl = site == i ? al : al * r + k;
+                const int nr = site == j ? be : be * r + k;
+                nA.at(nl, o, s, nr) = v;
+              }
+      A = std::move(nA);
+    }
+    compress_mpo(T);
+    for (int site = i; site < j; ++site)
+      if (T[site].wr > TNMPS_MAX_MPO_BOND) {
+        err = "super-gate MPO bond above " + std::to_string(TNMPS_MAX_MPO_BOND);
+        return TNMPS_ERR_UNSUPPORTED;
+      }
+  }
+  sg.w.assign(m + 1, 1);
+  sg.woff.assign(m, 0);
+  sg.W.clear();
+  for (int i = 0; i < m; ++i) {
+    sg.woff[i] = (int64_t)sg.W.size();
+    sg.w[i + 1] = i + 1 < m ? T[i].wr : 1;
+    sg.W.insert(sg.W.end(), T[i].t.begin(), T[i].t.end());
+  }
+  return TNMPS_OK;
 }
 
 }  // namespace
@@ -689,6 +904,288 @@ tnmps_status tnmps_sample_dev(tnmps_ctx *c, const double *uniforms_dev, int shot
   if ((st = move_centre(c, c->n - 1)) != TNMPS_OK) return st;
   cudaError_t e = launch_sample(c, uniforms_dev, shots, bits_dev);
   return e == cudaSuccess ? TNMPS_OK : cuda_fail(c, e, "sample");
+}
+
+// ---------------------------------------------------------- super-gates
+tnmps_status tnmps_supergate_create(tnmps_supergate **out, int n, const tnmps_gate *gates,
+                                    size_t n_gates, const double *theta, size_t n_params) {
+  if (!out) return TNMPS_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || n_gates == 0 || !gates || (n_params && !theta)) return TNMPS_ERR_ARG;
+  tnmps_supergate *sg = new (std::nothrow) tnmps_supergate();
+  if (!sg) return TNMPS_ERR_NOMEM;
+  sg->n = n;
+  sg->p = n;
+  sg->q = -1;
+  for (size_t k = 0; k < n_gates; ++k) {
+    tnmps_gate g = gates[k];
+    const bool two = is_2q(g.op);
+    if ((!two && !is_1q(g.op)) || g.q0 < 0 || g.q0 >= n ||
+        (two && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)) ||
+        (g.param >= 0 && (size_t)g.param >= n_params)) {
+      delete sg;
+      return TNMPS_ERR_ARG;
+    }
+    if (g.param >= 0) {  // bind the parameter: a fixed-angle rotation
+      g.angle += g.scale * theta[g.param];
+      g.param = -1;
+      g.scale = 1;
+    }
+    if (!two) g.q1 = -1;
+    sg->p = std::min(sg->p, two ? std::min(g.q0, g.q1) : g.q0);
+    sg->q = std::max(sg->q, two ? std::max(g.q0, g.q1) : g.q0);
+    sg->gates.push_back(g);
+  }
+  std::string err;
+  tnmps_status st = build_supergate(*sg, err);
+  if (st != TNMPS_OK) {
+    delete sg;
+    return st;
+  }
+  *out = sg;
+  return TNMPS_OK;
+}
+
+void tnmps_supergate_free(tnmps_supergate *sg) { delete sg; }
+
+tnmps_status tnmps_supergate_info(const tnmps_supergate *sg, int32_t *first, int32_t *last,
+                                  int32_t *bonds) {
+  if (!sg) return TNMPS_ERR_ARG;
+  if (first) *first = sg->p;
+  if (last) *last = sg->q;
+  if (bonds)
+    for (size_t i = 0; i < sg->w.size(); ++i) bonds[i] = sg->w[i];
+  return TNMPS_OK;
+}
+
+tnmps_status tnmps_supergate_mpo(const tnmps_supergate *sg, double *out, size_t cap) {
+  if (!sg || !out) return TNMPS_ERR_ARG;
+  if (cap < 2 * sg->W.size()) return TNMPS_ERR_NOMEM;
+  for (size_t e = 0; e < sg->W.size(); ++e) {
+    out[2 * e] = sg->W[e].real();
+    out[2 * e + 1] = sg->W[e].imag();
+  }
+  return TNMPS_OK;
+}
+
+namespace {
+
+// Workspace of a fit: psi snapshot, psi dims, MPO, environments, three
+// scratch buffers, overlaps and the saved discarded weights.
+struct FitLayout {
+  size_t psi, pdims, mpo, env, s1, s2, s3, ov, saved, total;
+  int64_t psi_stride, env_stride, s_stride;
+  std::vector<int64_t> env_off;
+};
+
+FitLayout fit_layout(const tnmps_ctx *c, const tnmps_supergate *sg) {
+  FitLayout L;
+  const size_t esz = c->dtype == TNMPS_C128 ? 16 : 8;
+  const int p = sg->p, q = sg->q, B = c->batch;
+  const int64_t end = q + 1 < c->n ? c->site_off[q + 1] : c->state_elems;
+  L.psi_stride = end - c->site_off[p];
+  auto cap = [&](int dims_index) { return (int64_t)c->cap[dims_index]; };
+  auto w = [&](int bond) { return (int64_t)sg->w[bond + 1 - p]; };  // bonds p-1..q
+  L.env_stride = 0;
+  for (int b = p - 1; b <= q; ++b) {
+    L.env_off.push_back(L.env_stride);
+    L.env_stride += cap(b + 1) * w(b) * cap(b + 1);
+    L.env_stride = (L.env_stride + 31) & ~(int64_t)31;
+  }
+  int64_t s = 0;
+  for (int i = p; i <= q; ++i) {
+    const int64_t Ca = cap(i), Cm = cap(i + 1), wa = w(i - 1), wm = w(i);
+    s = std::max(s, Ca * wa * 2 * Cm);   // T1
+    s = std::max(s, Ca * 2 * wm * Cm);   // T2
+    s = std::max(s, 2 * Ca * Cm * wm);   // V1
+    s = std::max(s, 2 * Cm * wa * Ca);   // V2
+    if (i < q) {
+      const int64_t Cc = cap(i + 2), wc = w(i + 1);
+      s = std::max(s, Ca * 2 * wm * 2 * Cc);  // T3
+      s = std::max(s, 4 * Ca * wc * Cc);      // T4
+    }
+  }
+  L.s_stride = (s + 31) & ~(int64_t)31;
+  size_t o = 0;
+  L.psi = o;
+  o = al256(o + esz * B * L.psi_stride);
+  L.pdims = o;
+  o = al256(o + 4 * (size_t)B * (c->n + 1));
+  L.mpo = o;
+  o = al256(o + esz * sg->W.size());
+  L.env = o;
+  o = al256(o + esz * B * L.env_stride);
+  L.s1 = o;
+  o = al256(o + esz * B * L.s_stride);
+  L.s2 = o;
+  o = al256(o + esz * B * L.s_stride);
+  L.s3 = o;
+  o = al256(o + esz * B * L.s_stride);
+  L.ov = o;
+  o = al256(o + 16 * (size_t)B);
+  L.saved = o;
+  o = al256(o + 8 * (size_t)B);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+size_t tnmps_supergate_workspace_bytes(const tnmps_ctx *c, const tnmps_supergate *sg) {
+  if (!c || !sg || sg->n != c->n) return 0;
+  return fit_layout(c, sg).total;
+}
+
+tnmps_status tnmps_apply_supergate(tnmps_ctx *c, const tnmps_supergate *sg, int chi_max,
+                                   double target, double tol, int max_sweeps, void *ws,
+                                   size_t ws_bytes, double *fidelity, double *fidelity_start,
+                                   int32_t *info) {
+  if (!c) return TNMPS_ERR_ARG;
+  if (!sg || sg->n != c->n) return fail(c, TNMPS_ERR_ARG, "super-gate for another register");
+  if (chi_max < 1 || chi_max > c->chi) return fail(c, TNMPS_ERR_ARG, "chi_max outside 1..chi");
+  if (max_sweeps < 1) return fail(c, TNMPS_ERR_ARG, "max_sweeps < 1");
+  tnmps_status st = inject(c);
+  if (st != TNMPS_OK) return st;
+  const int B = c->batch, p = sg->p, q = sg->q;
+  std::vector<double> F(B, 1.0), F0(B, 1.0), Fprev(B, 0.0), ovh(2 * (size_t)B);
+  int sweeps = 0, stages = 0, chi = 0;
+  auto outputs = [&]() {
+    if (fidelity) std::copy(F.begin(), F.end(), fidelity);
+    if (fidelity_start) std::copy(F0.begin(), F0.end(), fidelity_start);
+    if (info) {
+      info[0] = sweeps;
+      info[1] = stages;
+      info[2] = chi;
+    }
+  };
+  if (p == q) {  // one qubit: the gates apply exactly
+    if ((st = run_circuit(c, sg->gates.data(), sg->gates.size(), nullptr, 0, 0)) != TNMPS_OK)
+      return st;
+    if ((st = sync_check(c)) != TNMPS_OK) return st;
+    outputs();
+    return TNMPS_OK;
+  }
+  const FitLayout L = fit_layout(c, sg);
+  if (!ws) return fail(c, TNMPS_ERR_ARG, "null workspace");
+  if (ws_bytes < L.total) return fail(c, TNMPS_ERR_NOMEM, "super-gate workspace too small");
+  if ((st = move_centre(c, p)) != TNMPS_OK) return st;
+  char *w8 = static_cast<char *>(ws);
+  const size_t esz = c->dtype == TNMPS_C128 ? 16 : 8;
+  FitDev f;
+  f.p = p;
+  f.q = q;
+  f.psi = w8 + L.psi;
+  f.psi_stride = L.psi_stride;
+  f.psi_base = c->site_off[p];
+  f.pdims = reinterpret_cast<const int32_t *>(w8 + L.pdims);
+  f.s1 = w8 + L.s1;
+  f.s2 = w8 + L.s2;
+  f.s3 = w8 + L.s3;
+  f.s_stride = L.s_stride;
+  f.env = w8 + L.env;
+  f.env_stride = L.env_stride;
+  f.mpo = w8 + L.mpo;
+  f.mpo_off = sg->woff;
+  f.w = sg->w;
+  f.env_off = L.env_off;
+  f.pub = c->ub;
+  double *ov = reinterpret_cast<double *>(w8 + L.ov);
+  double *saved = reinterpret_cast<double *>(w8 + L.saved);
+  // MPO in the context's precision (host copy kept alive until the first sync)
+  std::vector<double> mpo_d;
+  std::vector<float> mpo_f;
+  const void *mpo_src;
+  if (c->dtype == TNMPS_C128) {
+    mpo_d.resize(2 * sg->W.size());
+    for (size_t e = 0; e < sg->W.size(); ++e) {
+      mpo_d[2 * e] = sg->W[e].real();
+      mpo_d[2 * e + 1] = sg->W[e].imag();
+    }
+    mpo_src = mpo_d.data();
+  } else {
+    mpo_f.resize(2 * sg->W.size());
+    for (size_t e = 0; e < sg->W.size(); ++e) {
+      mpo_f[2 * e] = (float)sg->W[e].real();
+      mpo_f[2 * e + 1] = (float)sg->W[e].imag();
+    }
+    mpo_src = mpo_f.data();
+  }
+  char *sites = static_cast<char *>(c->sites);
+  const size_t row = esz * (size_t)L.psi_stride, pitch = esz * (size_t)c->state_elems;
+  cudaError_t e = cudaMemcpyAsync(w8 + L.mpo, mpo_src, esz * sg->W.size(),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(w8 + L.psi, row, sites + esz * c->site_off[p], pitch, row, B,
+                          cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w8 + L.pdims, c->dims, 4 * (size_t)B * (c->n + 1),
+                        cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(saved, c->discarded, 8 * (size_t)B, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "super-gate snapshot");
+  const std::vector<int> ub0 = c->ub;
+  // step (6) starts from the bonds of the copy of step (3)
+  chi = 1;
+  for (int b = p; b < q; ++b) chi = std::max(chi, c->ub[b + 1]);
+  chi = std::min(chi, chi_max);
+  auto read_fidelity = [&](std::vector<double> &out) -> tnmps_status {
+    cudaError_t e2 = cudaMemcpyAsync(ovh.data(), ov, 16 * (size_t)B, cudaMemcpyDeviceToHost,
+                                     c->stream);
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "read overlaps");
+    tnmps_status s2 = sync_check(c);
+    if (s2 != TNMPS_OK) return s2;
+    for (int b = 0; b < B; ++b) out[b] = ovh[2 * b] * ovh[2 * b] + ovh[2 * b + 1] * ovh[2 * b + 1];
+    return TNMPS_OK;
+  };
+  for (;;) {
+    ++stages;
+    if (stages > 1) {  // back to the copy of psi
+      e = cudaMemcpy2DAsync(sites + esz * c->site_off[p], pitch, w8 + L.psi, row, row, B,
+                            cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->dims, w8 + L.pdims, 4 * (size_t)B * (c->n + 1),
+                            cudaMemcpyDeviceToDevice, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "super-gate restore");
+      c->ub = ub0;
+      c->centre = p;
+    }
+    // first iterate: the gates one by one under the stage's bond cap
+    c->fit_cap = chi;
+    st = run_circuit(c, sg->gates.data(), sg->gates.size(), nullptr, 0, 0);
+    if (st == TNMPS_OK && (e = fit_overlap(c, f, ov)) != cudaSuccess)
+      st = cuda_fail(c, e, "super-gate overlap");
+    if (st == TNMPS_OK) st = read_fidelity(F0);
+    if (st != TNMPS_OK) {
+      c->fit_cap = 0;
+      return st;
+    }
+    F = F0;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+      if ((st = move_centre(c, p)) == TNMPS_OK) {
+        if ((e = fit_sweep(c, f, ov)) != cudaSuccess) st = cuda_fail(c, e, "super-gate sweep");
+        c->centre = q;
+      }
+      if (st == TNMPS_OK) st = read_fidelity(F);
+      if (st != TNMPS_OK) {
+        c->fit_cap = 0;
+        return st;
+      }
+      ++sweeps;
+      double gain = -1e300;
+      for (int b = 0; b < B; ++b) gain = std::max(gain, F[b] - Fprev[b]);
+      if (sw > 0 && gain < tol) break;
+      Fprev = F;
+    }
+    double worst = 0;
+    for (int b = 0; b < B; ++b) worst = std::max(worst, 1.0 - F[b]);
+    if (worst <= target || chi >= chi_max) break;
+    chi = std::min(chi_max, 2 * chi);
+  }
+  c->fit_cap = 0;
+  if ((e = fit_finish(c, saved, ov)) != cudaSuccess) return cuda_fail(c, e, "super-gate finish");
+  if ((st = sync_check(c)) != TNMPS_OK) return st;
+  outputs();
+  return TNMPS_OK;
 }
 
 tnmps_status tnmps_check(tnmps_ctx *c) {

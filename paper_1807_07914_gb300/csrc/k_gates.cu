@@ -14,6 +14,8 @@
 // the column index of (s, c) is s*D + c. Theta is row-major (2 D_{l-1}) x
 // (2 D_{l+1}) in theta_buf; its column-major copy in w_buf is the Jacobi
 // input.
+#include <string.h>
+
 #include "gate_dev.cuh"
 #include "gates_dev.cuh"
 #include "gemm_tile.cuh"
@@ -404,6 +406,10 @@ __global__ void k_set_bond(StateView v, int bond, const int32_t *newdim) {
 }
 
 template <typename R>
+cudaError_t split_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t ths,
+                       cudaEvent_t ev);
+
+template <typename R>
 cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t ths) {
   const StateView v = c->view();
   const int l = op.l;
@@ -424,6 +430,22 @@ cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
     if ((e = launch_gemm<R>(pt, Mmax, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
       return e;
   }
+  return split_impl<R>(c, op, theta, ths, ev);
+}
+
+// G applied to the block in theta_buf (row-major, 2D_{l-1} x 2D_{l+1}), then
+// K3 (Jacobi) and K4 (rank by rule R under the bond cap, A_l <- U_k,
+// C_{l+1} <- U_k^H Theta, normalised); the centre ends on l+1. ev: open
+// PC_THETA timing event of the caller (or null).
+template <typename R>
+cudaError_t split_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t ths,
+                       cudaEvent_t ev) {
+  const StateView v = c->view();
+  const int l = op.l;
+  const int Mmax = 2 * c->ub[l], Nmax = 2 * c->ub[l + 2];
+  cx<R> *tb = reinterpret_cast<cx<R> *>(c->theta_buf);
+  cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
+  cudaError_t e;
   {
     dim3 grid((c->ub[l + 2] + 31) / 32, (c->ub[l] + 15) / 16, c->batch);
     k_apply_gate4<R><<<grid, 256, 0, c->stream>>>(v, op, theta, ths, tb, wb, c->tw);
@@ -440,12 +462,14 @@ cudaError_t gate2_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
   ev = prof_begin(c, PC_SPLIT);
   const double floor_eps =
       c->dtype != TNMPS_C128 ? 8.0 * 5.9604644775390625e-08 : 8.0 * 1.1102230246251565e-16;
-  k_split_select<R><<<c->batch, 256, 0, c->stream>>>(v, l, wb, c->tw, c->eps, floor_eps,
-                                                      c->cap[l + 1], c->discarded, c->scale,
-                                                      c->err, c->counters);
+  int cap = c->cap[l + 1];
+  if (c->fit_cap > 0 && c->fit_cap < cap) cap = c->fit_cap;
+  k_split_select<R><<<c->batch, 256, 0, c->stream>>>(v, l, wb, c->tw, c->eps, floor_eps, cap,
+                                                      c->discarded, c->scale, c->err,
+                                                      c->counters);
   ++c->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int kub = c->cap[l + 1];
+  int kub = cap;
   kub = kub < Mmax ? kub : Mmax;
   kub = kub < Nmax ? kub : Nmax;
   if (sizeof(R) == 4) {
@@ -560,6 +584,15 @@ cudaError_t launch_init_state(tnmps_ctx *c) {
 cudaError_t launch_gate2(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t ths) {
   return c->dtype == TNMPS_C128 ? gate2_impl<double>(c, op, theta, ths)
                                 : gate2_impl<float>(c, op, theta, ths);
+}
+
+cudaError_t launch_split_theta(tnmps_ctx *c, int l) {
+  Op2 op;
+  memset(&op, 0, sizeof op);
+  op.l = l;
+  for (int d = 0; d < 4; ++d) op.core[2 * (4 * d + d)] = 1.0;  // identity 4x4
+  return c->dtype == TNMPS_C128 ? split_impl<double>(c, op, nullptr, 0, nullptr)
+                                : split_impl<float>(c, op, nullptr, 0, nullptr);
 }
 
 cudaError_t launch_gate1(tnmps_ctx *c, const Op1 &op, const double *theta, int64_t ths) {

@@ -45,6 +45,7 @@ __host__ __device__ __forceinline__ void cfma(cx<R> &acc, cx<R> a, cx<R> b) {
 // ---------------------------------------------------------------- limits
 #define TNMPS_MAX_CHI 256
 #define TNMPS_MAX_FAC 8          // fused single-qubit factors per side of one op
+#define TNMPS_MAX_MPO_BOND 64    // super-gate MPO bond cap (after compression)
 #define TNMPS_JACOBI_MAX_DIM 512
 
 // device error flag bits
@@ -67,7 +68,9 @@ enum {
 };
 
 // kernel classes for event timing (mirrors tnmps_prof_class in tnmps.h)
-enum { PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_ENV_TC, PC_NUM };
+enum {
+  PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_ENV_TC, PC_FIT, PC_NUM
+};
 
 // ---------------------------------------------------------------- ops
 // A single-qubit factor: fixed 2x2 (kind 0, row-major complex in m[]) or a
@@ -162,6 +165,7 @@ struct tnmps_ctx {
 
   // host-side planning state; centre -1 = product state (any site may be the centre)
   int centre = -1;
+  int fit_cap = 0;                // > 0: extra bond cap of the splits (super-gate fit stages)
   std::vector<int> ub;            // upper bound of dims per bond index 0..n
   std::string last_error;
   int inject_nth = 0;
@@ -215,6 +219,9 @@ inline void prof_end(tnmps_ctx *c, int cls, cudaEvent_t a) {
 cudaError_t launch_init_state(tnmps_ctx *c);
 cudaError_t launch_gate2(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t th_stride);
 cudaError_t launch_gate1(tnmps_ctx *c, const Op1 &op, const double *theta, int64_t th_stride);
+// K3 + K4 on the block already in theta_buf (identity gate): rank under the
+// bond cap, A_l <- U_k, C_{l+1} <- U_k^H Theta normalised; centre to l+1
+cudaError_t launch_split_theta(tnmps_ctx *c, int l);
 cudaError_t launch_move_right(tnmps_ctx *c, int site);
 cudaError_t launch_move_left(tnmps_ctx *c, int site);
 // Measurement shots (centre on site n-1): u [batch][shots][n] -> bits
@@ -227,6 +234,31 @@ int64_t theta_tc_b_bytes(int chi);
 cudaError_t launch_jacobi_standalone(tnmps_dtype dt, int batch, int m, int n, void *a, int lda,
                                      double *sigma, int32_t *sweeps, int max_sweeps,
                                      cudaStream_t s);
+
+// Super-gate fit over the window [p, q] (device buffers carved from the
+// caller's workspace; element counts in the context's complex type).
+struct FitDev {
+  int p = 0, q = 0;
+  const void *psi = nullptr;      // snapshot of psi's window sites, per state psi_stride
+  int64_t psi_stride = 0, psi_base = 0;  // psi_base = site_off[p]
+  const int32_t *pdims = nullptr; // [batch][n+1] psi dims
+  void *s1 = nullptr, *s2 = nullptr, *s3 = nullptr;  // scratch, per state s_stride
+  int64_t s_stride = 0;
+  void *env = nullptr;            // environment slots of bonds p-1..q, per state env_stride
+  int64_t env_stride = 0;
+  const void *mpo = nullptr;      // MPO tensors [w_{i-1}][2][2][w_i], sites p..q
+  std::vector<int64_t> mpo_off;   // per window site
+  std::vector<int> w;             // MPO bonds, w[0] = w[q-p+1] = 1
+  std::vector<int64_t> env_off;   // per bond p-1..q
+  std::vector<int> pub;           // upper bounds of psi dims, size n+1
+};
+// <phi|G psi> over the window into ov[batch][2] (FP64 re, im)
+cudaError_t fit_overlap(tnmps_ctx *c, const FitDev &f, double *ov);
+// one left-to-right sweep of two-site updates (centre on p before, on q
+// after); ov receives <phi|G psi> after the sweep
+cudaError_t fit_sweep(tnmps_ctx *c, const FitDev &f, double *ov);
+// discarded = saved + max(0, 1 - |ov|^2)
+cudaError_t fit_finish(tnmps_ctx *c, const double *saved, const double *ov);
 
 // expectation plan (built on the host)
 struct TermPlan {

@@ -46,7 +46,7 @@ class Stats(C.Structure):
                                           "launches")]
 
 
-PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term", "env_tc")
+PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term", "env_tc", "fit")
 
 
 _lib = None
@@ -92,6 +92,12 @@ def lib():
         "tnmps_debug_inject": (I, [P, I, I]),
         "tnmps_expect_pauli_sum_noalloc": (I, [P, P, P, P]),
         "tnmps_sample_dev": (I, [P, P, I, P]),
+        "tnmps_supergate_create": (I, [C.POINTER(P), I, P, S, P, S]),
+        "tnmps_supergate_free": (None, [P]),
+        "tnmps_supergate_info": (I, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P]),
+        "tnmps_supergate_mpo": (I, [P, P, S]),
+        "tnmps_supergate_workspace_bytes": (S, [P, P]),
+        "tnmps_apply_supergate": (I, [P, P, I, D, D, I, P, S, P, P, P]),
         "tnmps_gemm_bf16_dev": (I, [I, I, I, P, I, P, I, P, I, P]),
         "tnmps_mlp_bytes": (S, [I, I, I]),
         "tnmps_mlp_num_params": (C.c_int64, [I, I]),
@@ -174,6 +180,51 @@ class PauliSum:
     __del__ = close
 
 
+class Supergate:
+    """An ordered aggregate of gates on any qubits, bound to parameter values,
+    held by the library as a matrix-product operator over the qubits it
+    touches (host side; no device work)."""
+
+    def __init__(self, n_qubits, circuit, theta=None):
+        self.n = int(n_qubits)
+        th = np.ascontiguousarray(theta if theta is not None else [0.0], dtype=np.float64)
+        arr = gate_array(circuit)
+        h = C.c_void_p()
+        st = lib().tnmps_supergate_create(C.byref(h), self.n, arr, len(circuit), _ptr(th),
+                                          0 if theta is None else th.size)
+        if st != 0:
+            raise TnmpsError(st, "invalid super-gate")
+        self._h = h
+        first, last = C.c_int32(), C.c_int32()
+        lib().tnmps_supergate_info(h, C.byref(first), C.byref(last), None)
+        self.first, self.last = first.value, last.value
+        bonds = np.zeros(self.last - self.first + 2, np.int32)
+        lib().tnmps_supergate_info(h, None, None, _ptr(bonds))
+        self.bonds = bonds
+
+    def mpo(self):
+        """The MPO site tensors [w_left, 2 out, 2 in, w_right], complex128."""
+        w = self.bonds
+        sizes = [int(w[i]) * 4 * int(w[i + 1]) for i in range(len(w) - 1)]
+        buf = np.zeros(2 * sum(sizes), np.float64)
+        st = lib().tnmps_supergate_mpo(self._h, _ptr(buf), buf.size)
+        if st != 0:
+            raise TnmpsError(st, "MPO read failed")
+        z = buf.view(np.complex128)
+        out, o = [], 0
+        for i, n in enumerate(sizes):
+            out.append(z[o:o + n].reshape(int(w[i]), 2, 2, int(w[i + 1])).copy())
+            o += n
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tnmps_supergate_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+
 def _csr(terms):
     off = [0]
     s, p, c = [], [], []
@@ -209,6 +260,7 @@ class MPSBatch:
             raise TnmpsError(st, "init failed")
         self._h = h
         self._ws = {}
+        self._sg_ws = None
         self.set_stream()
         self.set_cutoff(eps)
 
@@ -311,6 +363,25 @@ class MPSBatch:
         self.sample_dev(u, bits)
         self.check()
         return bits.cpu().numpy()
+
+    # -------------------------------------------------------------- super-gates
+    def apply_supergate(self, sg, chi_max=None, target=1e-10, tol=1e-12, max_sweeps=8):
+        """Apply a Supergate by overlap maximisation (synchronous). Returns
+        (fidelity [batch], fidelity of the first iterate [batch],
+        {"sweeps", "stages", "chi"})."""
+        nb = lib().tnmps_supergate_workspace_bytes(self._h, sg._h)
+        if nb == 0:
+            raise TnmpsError(1, "super-gate workspace query failed")
+        if self._sg_ws is None or self._sg_ws.numel() < nb:
+            self._sg_ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        f = np.zeros(self.batch, np.float64)
+        f0 = np.zeros(self.batch, np.float64)
+        info = np.zeros(3, np.int32)
+        self._check(lib().tnmps_apply_supergate(
+            self._h, sg._h, int(chi_max if chi_max is not None else self.chi), float(target),
+            float(tol), int(max_sweeps), _ptr(self._sg_ws), self._sg_ws.numel(), _ptr(f),
+            _ptr(f0), _ptr(info)))
+        return f, f0, {"sweeps": int(info[0]), "stages": int(info[1]), "chi": int(info[2])}
 
     # -------------------------------------------------------------- inspection
     def check(self):
