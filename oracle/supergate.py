@@ -140,20 +140,30 @@ def mpo_dense(W):
 
 
 def _env_left(L, phi, W, psi):
-    # L'[b', beta, b] = sum L[a', alpha, a] conj(phi[a', o, b']) W[alpha, o, s, beta] psi[a, s, b]
-    return np.einsum("xya,xob,yosz,asc->bzc", L, phi.conj(), W, psi, optimize=True)
+    # L'[b', beta, b] = sum L[a', alpha, a] conj(phi[a', o, b']) W[alpha, o, s, beta] psi[a, s, b],
+    # summed one operand at a time (psi, then W, then phi)
+    t = np.einsum("xya,asc->xysc", L, psi, optimize=True)
+    t = np.einsum("xysc,yosz->xozc", t, W, optimize=True)
+    return np.einsum("xozc,xob->bzc", t, phi.conj(), optimize=True)
 
 
 def _env_right(R, phi, W, psi):
-    # R'[c', gamma, c] = sum conj(phi[c', o, d']) W[gamma, o, s, delta] psi[c, s, d] R[d', delta, d]
-    return np.einsum("xod,gosh,csy,dhy->xgc", phi.conj(), W, psi, R, optimize=True)
+    # R'[c', gamma, c] = sum conj(phi[c', o, d']) W[gamma, o, s, delta] psi[c, s, d] R[d', delta, d],
+    # summed one operand at a time (R, then W, then phi)
+    t = np.einsum("csy,dhy->csdh", psi, R, optimize=True)
+    t = np.einsum("csdh,gosh->cdgo", t, W, optimize=True)
+    return np.einsum("cdgo,xod->xgc", t, phi.conj(), optimize=True)
 
 
 def _theta_grad(L, W1, W2, psi1, psi2, R):
     # Theta[a', o1, o2, c'] = sum L[a', al, a] W1[al, o1, s1, be] W2[be, o2, s2, ga]
-    #                             psi1[a, s1, m] psi2[m, s2, c] R[c', ga, c]
-    return np.einsum("xya,yosb,bptg,asm,mtc,zgc->xopz", L, W1, W2, psi1, psi2, R,
-                     optimize=True)
+    #                             psi1[a, s1, m] psi2[m, s2, c] R[c', ga, c],
+    # summed one operand at a time (psi1, W1, psi2, W2, R)
+    t = np.einsum("xya,asm->xysm", L, psi1, optimize=True)
+    t = np.einsum("xysm,yosb->xobm", t, W1, optimize=True)
+    t = np.einsum("xobm,mtc->xobtc", t, psi2, optimize=True)
+    t = np.einsum("xobtc,bptg->xopgc", t, W2, optimize=True)
+    return np.einsum("xopgc,zgc->xopz", t, R, optimize=True)
 
 
 def apply_supergate(mps, circuit, theta, chi_max, target=1e-10, tol=1e-12, max_sweeps=8):

@@ -173,6 +173,18 @@ def batch_jobs(count, rng, n_range=(16, 64), depth_range=(2, 8), chi_range=(32, 
 
 
 # ---------------------------------------------------------------- workloads
+def supergate_block(first, rng):
+    """A super-gate on the six qubits first..first+5: distant and reversed
+    two-qubit gates, a SWAP and two parameterised rotations (angles drawn from
+    rng). Returns (gates, theta)."""
+    f = int(first)
+    gates = [("CNOT", f, f + 4, -1, 0.0, 1.0), ("RY", f + 2, -1, 0, 0.0, 1.0),
+             ("CZ", f + 5, f + 1, -1, 0.0, 1.0), ("H", f + 3, -1, -1, 0.0, 1.0),
+             ("CNOT", f + 1, f + 2, -1, 0.0, 1.0), ("SWAP", f + 3, f, -1, 0.0, 1.0),
+             ("RX", f + 4, -1, 1, 0.0, 1.0), ("CNOT", f + 5, f + 3, -1, 0.0, 1.0)]
+    return gates, rng.uniform(-np.pi, np.pi, 2)
+
+
 def workload(name, rep=0):
     """Named synthetic workloads. Returns a dict with n, chi_max, eps,
     circuit, n_params, thetas, terms (and extra term sets for the bench)."""
