@@ -306,6 +306,9 @@ class MPSBatch:
         """Asynchronous: gates_c from gate_array(), thetas_dev a float64 CUDA
         tensor [batch, n_params]."""
         assert thetas_dev.is_cuda and thetas_dev.dtype == torch.float64
+        assert thetas_dev.dim() == 2 and thetas_dev.shape[0] == self.batch, \
+            "thetas_dev must hold one row per state"
+        assert thetas_dev.is_contiguous()
         ng = len(gates_c) if n_gates is None else n_gates
         self._check(lib().tnmps_apply_circuit_batched_dev(self._h, gates_c, ng, _ptr(thetas_dev),
                                                           thetas_dev.shape[-1]))

@@ -3,6 +3,7 @@
   python -m paper_1807_07914_gb300.workloads large100 [--dtype c64_bf16split] [--oracle]
   python -m paper_1807_07914_gb300.workloads rounds [--circuits 10] [--eps 1e-4] [--chi 64]
   python -m paper_1807_07914_gb300.workloads sample [--shots 1024] [--batch 304]
+  python -m paper_1807_07914_gb300.workloads supergate [--batch 304] [--sweeps 3] [--oracle]
 
 ``large100``: the 100-qubit single state (6 Ry/Rz + CNOT-ladder layers, 1200
 parameters, chi_max 256, cutoff 1e-8) and its 5000 random strings of weight
@@ -19,6 +20,13 @@ per launch sequence, so small registers are launch-latency bound).
 
 ``sample``: measurement shots of all 40 qubits from the chi=128 benchmark
 states (10 ansatz layers), ``--shots`` per state: shots per second.
+
+``supergate``: a six-qubit super-gate (distant CNOT/CZ, a SWAP, rotations)
+applied by overlap maximisation (Sec. II general gate action) to the chi=128
+benchmark states at chi_max 128 with a fixed number of sweeps: fits per
+second, the fidelity of the first iterate (gates one by one with truncation)
+and after the sweeps, per-class time shares and the FP32 rate of the fit
+GEMMs; with ``--oracle`` the FP64 oracle fits state 0 (time and fidelities).
 """
 import argparse
 import json
@@ -137,9 +145,121 @@ def sample(a):
                       "mean_ones": float(bits.float().mean())}))
 
 
+def _fit_flops(F, P, w, p, q):
+    """Real flops of the fit GEMMs of one state: one overlap pass and one sweep
+    (8 flops per complex MAC). F, P: bond dimensions of phi and psi indexed by
+    bond + 1 (bond -1 .. n-1); phi's are those after the fit (a sweep after the
+    first sees them)."""
+    def wb(bond):
+        return int(w[bond + 1 - p])
+
+    f = lambda bond: int(F[bond + 1])
+    d = lambda bond: int(P[bond + 1])
+
+    def left(i):  # T1, T2, EnvL at site i
+        fa = f(i - 1)
+        return 8 * (fa * wb(i - 1) * 2 * d(i) * d(i - 1) + 2 * wb(i) * fa * d(i) * 2 * wb(i - 1) +
+                    f(i) * wb(i) * d(i) * 2 * fa)
+
+    def right(i):  # V1, V2, EnvR at site i
+        return 8 * (2 * d(i - 1) * f(i) * wb(i) * d(i) + 2 * wb(i - 1) * d(i - 1) * f(i) * 2 * wb(i) +
+                    f(i - 1) * wb(i - 1) * d(i - 1) * 2 * f(i))
+
+    def grad(i):  # T1..T4 and Theta at the pair (i, i+1)
+        fa = f(i - 1)
+        return 8 * (fa * wb(i - 1) * 2 * d(i) * d(i - 1) + 2 * wb(i) * fa * d(i) * 2 * wb(i - 1) +
+                    fa * 2 * wb(i) * 2 * d(i + 1) * d(i) +
+                    2 * wb(i + 1) * 2 * fa * d(i + 1) * 2 * wb(i) +
+                    4 * fa * f(i + 1) * wb(i + 1) * d(i + 1))
+
+    env_l = lambda i: 8 * f(i) * wb(i) * d(i) * 2 * f(i - 1)
+    overlap = sum(left(i) for i in range(p, q + 1))
+    sweep = (sum(right(i) for i in range(q, p + 1, -1)) +
+             sum(grad(i) + env_l(i) for i in range(p, q)) + left(q))
+    return overlap, sweep
+
+
+def supergate(a):
+    wl = inputs.workload("chi128")
+    B, P = a.batch, wl["n_params"]
+    th = inputs.thetas(B, P, inputs.rng_for(5, 12))
+    th[0] = wl["thetas"][0]  # the row the oracle fits
+    th = torch.tensor(th, dtype=torch.float64, device="cuda")
+    m = tnmps.MPSBatch(40, 128, B, dtype=a.dtype, max_params=P, eps=wl["eps"])
+    gates = tnmps.gate_array(wl["circuit"])
+    block, bth = inputs.supergate_block(a.first, inputs.rng_for(5, 11))
+    sg = tnmps.Supergate(40, block, bth)
+    kw = dict(chi_max=128, target=1e-10, tol=-1.0, max_sweeps=a.sweeps)
+
+    def fresh():
+        m.reset()
+        m.apply_circuit_dev(gates, th)
+        torch.cuda.synchronize()
+
+    def fit():  # the fit alone sits in an NVTX range (launch lists filter on it)
+        torch.cuda.nvtx.range_push("supergate_fit")
+        r = m.apply_supergate(sg, **kw)
+        torch.cuda.nvtx.range_pop()
+        return r
+
+    fresh()
+    psi_dims = np.concatenate([np.ones((B, 1), np.int64), m.bond_dims(), np.ones((B, 1), np.int64)], 1)
+    fit()  # warm-up
+    t_tot, F, F0 = 0.0, [], []
+    for _ in range(a.reps):
+        fresh()
+        t0 = time.perf_counter()
+        f, f0, info = fit()
+        t_tot += time.perf_counter() - t0
+        F.append(f)
+        F0.append(f0)
+    phi_dims = np.concatenate([np.ones((B, 1), np.int64), m.bond_dims(), np.ones((B, 1), np.int64)], 1)
+    win = phi_dims[:, sg.first:sg.last + 2]  # bonds first-1 .. last
+    fresh()  # one more run with per-class event timing
+    m.profile(tnmps.PROF_CLASSES)
+    t0 = time.perf_counter()
+    fit()
+    t_prof = time.perf_counter() - t0
+    prof = m.profile_read()
+    m.profile(None)
+    fit_flops = 0
+    for z in range(B):
+        ov, sw = _fit_flops(phi_dims[z], psi_dims[z], sg.bonds, sg.first, sg.last)
+        fit_flops += ov + a.sweeps * sw
+    fit_s = prof["fit"][0] / 1e3
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    F, F0 = np.concatenate(F), np.concatenate(F0)
+    out = {"workload": f"super-gate on qubits {sg.first}..{sg.last} (distant CNOT/CZ, SWAP, "
+                       f"rotations) of {B} chi=128 states (40 qubits, 10 layers), chi_max 128, "
+                       f"{a.sweeps} sweeps", "dtype": a.dtype, "batch": B, "reps": a.reps,
+           "mpo_bonds": [int(x) for x in sg.bonds],
+           "fits_per_s": B * a.reps / t_tot, "s_per_batch": t_tot / a.reps,
+           "fidelity_first_iterate_mean": float(F0.mean()), "fidelity_mean": float(F.mean()),
+           "window_bond_min_mean": [int(win.min()), float(win.mean())],
+           "class_share": {k: v[0] / 1e3 / t_prof for k, v in prof.items() if v[1]},
+           "fit_gemm": {"kernel": "k_gemm fit problems (FP32 CUDA-core tile GEMM)",
+                        "bound": "alu", "alg_flops": fit_flops, "seconds": fit_s,
+                        "achieved": fit_flops / fit_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": fit_flops / fit_s / 1e12 / peak,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}}
+    if a.oracle:
+        import copy
+
+        from oracle import mps as OM
+        from oracle import supergate as OSG
+        om = OM.MPS(40, 128, wl["eps"]).run(wl["circuit"], wl["thetas"][0])
+        t0 = time.perf_counter()
+        _, f_or, _, _, f0_or = OSG.apply_supergate(copy.deepcopy(om), block, bth, **kw)
+        out["oracle_s_per_fit"] = time.perf_counter() - t0
+        out["oracle_fits_per_s"] = 1.0 / out["oracle_s_per_fit"]
+        out["state0_fidelity_gpu_vs_oracle"] = [float(F[0]), float(f_or)]
+        out["state0_first_iterate_gpu_vs_oracle"] = [float(F0[0]), float(f0_or)]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("large100", "rounds", "sample"))
+    ap.add_argument("case", choices=("large100", "rounds", "sample", "supergate"))
     ap.add_argument("--shots", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--dtype", default="c64_bf16split", choices=tuple(ESIZE))
@@ -147,8 +267,11 @@ def main():
     ap.add_argument("--circuits", type=int, default=10)
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--chi", type=int, default=64)
+    ap.add_argument("--first", type=int, default=17, help="supergate: first qubit of the block")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=3)
     a = ap.parse_args()
-    {"large100": large100, "rounds": rounds, "sample": sample}[a.case](a)
+    {"large100": large100, "rounds": rounds, "sample": sample, "supergate": supergate}[a.case](a)
 
 
 if __name__ == "__main__":
