@@ -224,6 +224,39 @@ __device__ __forceinline__ void store_block(const cx<R> *__restrict__ S, cx<R> *
   }
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, generic proxy);
+// cp_async_wait_all completes the calling thread's copies.
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// load_block issued as asynchronous copies, with the thread <-> element map
+// of store_block (a thread overwrites only what it wrote back itself, so a
+// store_block / prefetch_block pair on one slot needs no barrier between).
+// The element-wise path (unaligned columns) copies synchronously.
+template <typename R>
+__device__ __forceinline__ void prefetch_block(cx<R> *__restrict__ S,
+                                               const cx<R> *__restrict__ W, const int *perm,
+                                               int col0, int ncol, int M, int ld, int Mp) {
+  if (vec_ok(W, M, ld)) {
+    constexpr int V = sizeof(cx<R>) == 8 ? 2 : 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nv = M / V;
+    for (int c = warp; c < ncol; c += nw) {
+      const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)perm[col0 + c] * ld);
+      float4 *dst = reinterpret_cast<float4 *>(S + c * Mp);
+      for (int v = lane; v < nv; v += 32) cp_async16(dst + v, src + v);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    return;
+  }
+  load_block(S, W, perm, col0, ncol, M, ld, Mp);
+}
+
 // A warp's share of one round: up to two disjoint pairs, processed together.
 // Two pairs at once only while both fit in registers (8E floats or 16E
 // doubles of column data per lane).
@@ -455,11 +488,13 @@ __device__ int cross_blocks(cx<R> *S0, int n0, cx<R> *S1, int n1, int M, int Mp,
 // whether the last sweep rotated nothing; *rotations / *checked count pair
 // visits (per thread: warps add their own). XREG: see cross_blocks (the CTA
 // must then have BC / 2 warps).
-template <typename R, int BC, int E, bool XREG = false>
+template <typename R, int BC, int E, bool XREG = false, bool PF = false>
 __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, float tolfac,
-                          int max_sweeps, bool *converged, int *rotations, int *checked) {
+                          int max_sweeps, bool *converged, int *rotations, int *checked,
+                          cx<R> *S2 = nullptr) {
   constexpr int Mp = 32 * E;
-  cx<R> *S[2] = {S0, S1};
+  constexpr int NS = PF ? 3 : 2;  // staging slots; PF: the third takes the next block early
+  cx<R> *S[3] = {S0, S1, S2};
   __shared__ int s_rot;
   __shared__ unsigned s_dmax;
   const R tol = R(tolfac) * (sqrt(R(M)) + R(16)) * Eps<R>::u();
@@ -486,7 +521,7 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
   }
   const R tiny = (R)((64.0 * (double)Eps<R>::u() * (double)Eps<R>::u()) * s_fro[0]);
   const int nb = (N + BC - 1) / BC;
-  int held[2] = {-1, -1};
+  int held[3] = {-1, -1, -1};
   // column order of the sweep: the blocks are groups of BC consecutive
   // entries of s_perm (matrix columns sorted by descending norm each sweep)
   __shared__ int s_perm[TNMPS_JACOBI_MAX_DIM];
@@ -511,7 +546,7 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
   while (sweep < max_sweeps) {
     // de Rijk ordering: every sweep visits the columns by descending norm
     // (staged blocks written back first; ties keep the index order)
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < NS; ++s)
       if (held[s] >= 0) {
         store_block(S[s], W, s_perm, held[s] * BC, min(BC, N - held[s] * BC), M, ld, Mp);
         held[s] = -1;
@@ -547,16 +582,66 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
     __syncthreads();
     int rot = 0;
     R dmax2 = 0;
-    for (int I = 0; I < nb; ++I) {
-      int sI = (held[1] == I) ? 1 : 0;
-      ensure(sI, I);
-      const int nI = min(BC, N - I * BC);
-      rot += within_block<R, E>(S[sI], nI, M, Mp, tol2, tiny, chk, dmax2);
-      for (int J = I + 1; J < nb; ++J) {
-        ensure(1 - sI, J);
-        const int nJ = min(BC, N - J * BC);
-        rot += cross_blocks<R, E, BC, XREG>(S[sI], nI, S[1 - sI], nJ, M, Mp, tol2, tiny, chk,
-                                            dmax2);
+    if constexpr (PF) {
+      // steps (I, I), (I, I+1), ..., (I, nb-1), (I+1, I+1), ...: each step
+      // needs at most one block that is not staged yet, which is copied into
+      // the slot neither this step nor the next uses (written back first)
+      // while this step computes
+      auto slot_of = [&](int blk) {
+        for (int s = 0; s < 3; ++s)
+          if (held[s] == blk) return s;
+        return -1;
+      };
+      load_block(S[0], W, s_perm, 0, min(BC, N), M, ld, Mp);
+      held[0] = 0;
+      __syncthreads();
+      int I = 0, J = 0;
+      for (;;) {
+        int nI = I, nJ = J + 1;
+        if (nJ >= nb) {
+          nI = I + 1;
+          nJ = nI;
+        }
+        const bool more = nI < nb;
+        const int sX = slot_of(I), sY = slot_of(J);
+        if (more) {
+          const int need = slot_of(nI) < 0 ? nI : (slot_of(nJ) < 0 ? nJ : -1);
+          if (need >= 0) {
+            int t = -1;  // empty slot first, then the lowest block (done for this sweep)
+            for (int s = 0; s < 3; ++s) {
+              if (s == sX || s == sY || held[s] == nI || held[s] == nJ) continue;
+              if (t < 0 || held[s] < held[t]) t = s;
+            }
+            if (held[t] >= 0)
+              store_block(S[t], W, s_perm, held[t] * BC, min(BC, N - held[t] * BC), M, ld, Mp);
+            prefetch_block(S[t], W, s_perm, need * BC, min(BC, N - need * BC), M, ld, Mp);
+            held[t] = need;
+          }
+        }
+        const int nX = min(BC, N - I * BC);
+        if (I == J)
+          rot += within_block<R, E>(S[sX], nX, M, Mp, tol2, tiny, chk, dmax2);
+        else
+          rot += cross_blocks<R, E, BC, XREG>(S[sX], nX, S[sY], min(BC, N - J * BC), M, Mp,
+                                              tol2, tiny, chk, dmax2);
+        cp_async_wait_all();
+        __syncthreads();
+        if (!more) break;
+        I = nI;
+        J = nJ;
+      }
+    } else {
+      for (int I = 0; I < nb; ++I) {
+        int sI = (held[1] == I) ? 1 : 0;
+        ensure(sI, I);
+        const int nI = min(BC, N - I * BC);
+        rot += within_block<R, E>(S[sI], nI, M, Mp, tol2, tiny, chk, dmax2);
+        for (int J = I + 1; J < nb; ++J) {
+          ensure(1 - sI, J);
+          const int nJ = min(BC, N - J * BC);
+          rot += cross_blocks<R, E, BC, XREG>(S[sI], nI, S[1 - sI], nJ, M, Mp, tol2, tiny, chk,
+                                              dmax2);
+        }
       }
     }
     if (rot && (threadIdx.x & 31) == 0) {
@@ -581,7 +666,7 @@ __device__ int jacobi_run(cx<R> *W, int M, int N, int ld, cx<R> *S0, cx<R> *S1, 
       break;
     }
   }
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < NS; ++s)
     if (held[s] >= 0)
       store_block(S[s], W, s_perm, held[s] * BC, min(BC, N - held[s] * BC), M, ld, Mp);
   __syncthreads();

@@ -39,7 +39,7 @@ struct JacobiArgs {
   unsigned long long *counters;
 };
 
-template <typename R, int BC, int E, int NT, int MINB>
+template <typename R, int BC, int E, int NT, int MINB, bool PF>
 __global__ void __launch_bounds__(NT, MINB) k_jacobi(JacobiArgs p) {
   const int b = blockIdx.x;
   int M, N, ld;
@@ -56,12 +56,14 @@ __global__ void __launch_bounds__(NT, MINB) k_jacobi(JacobiArgs p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *S0 = reinterpret_cast<cx<R> *>(smraw);
   cx<R> *S1 = S0 + BC * 32 * E;
+  cx<R> *S2 = PF ? S1 + BC * 32 * E : nullptr;
   bool converged;
   int total_rot, checked;
   // x columns of the cross rounds in registers when the CTA has BC / 2 warps
   constexpr bool XREG = jac::TwoPairs<R, E>::ok && NT == 16 * BC;
-  const int sweep = jac::jacobi_run<R, BC, E, XREG>(W, M, N, ld, S0, S1, p.tolfac, p.max_sweeps,
-                                                    &converged, &total_rot, &checked);
+  const int sweep = jac::jacobi_run<R, BC, E, XREG, PF>(W, M, N, ld, S0, S1, p.tolfac,
+                                                        p.max_sweeps, &converged, &total_rot,
+                                                        &checked, S2);
   if (p.sigma_out) {  // column norms in FP64
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = warp; j < N; j += nw) {
@@ -88,14 +90,16 @@ __global__ void __launch_bounds__(NT, MINB) k_jacobi(JacobiArgs p) {
   }
 }
 
-// NT threads (XREG when NT = 16 BC); MINB CTAs per SM
-template <typename R, int BC, int E, int NT = (BC >= 16 ? 512 : 256), int MINB = 1>
+// NT threads (XREG when NT = 16 BC); MINB CTAs per SM; PF: three staging
+// slots, the next block copied asynchronously while the current step computes
+template <typename R, int BC, int E, int NT = (BC >= 16 ? 512 : 256), int MINB = 1,
+          bool PF = false>
 cudaError_t run(const JacobiArgs &a, int batch, cudaStream_t s) {
-  const size_t smem = (size_t)2 * BC * 32 * E * sizeof(cx<R>);
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, BC, E, NT, MINB>,
+  const size_t smem = (size_t)(PF ? 3 : 2) * BC * 32 * E * sizeof(cx<R>);
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, BC, E, NT, MINB, PF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi<R, BC, E, NT, MINB><<<batch, NT, smem, s>>>(a);
+  k_jacobi<R, BC, E, NT, MINB, PF><<<batch, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -104,7 +108,7 @@ cudaError_t dispatch(const JacobiArgs &a, int Mcap, int batch, cudaStream_t s) {
   if (Mcap <= 64) return run<R, 32, 2>(a, batch, s);
   if (Mcap <= 128) return run<R, 32, 4>(a, batch, s);
   if constexpr (sizeof(R) == 4)  // 16-column blocks, 8 warps, two CTAs per SM
-    if (Mcap <= 256) return run<R, 16, 8, 256, 2>(a, batch, s);
+    if (Mcap <= 256) return run<R, 16, 8, 256, 2, true>(a, batch, s);
   if (Mcap <= 256) return run<R, sizeof(R) == 8 ? 16 : 32, 8>(a, batch, s);
   return run<R, sizeof(R) == 8 ? 8 : 16, 16>(a, batch, s);
 }
