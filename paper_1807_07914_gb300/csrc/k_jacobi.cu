@@ -105,12 +105,12 @@ cudaError_t run(const JacobiArgs &a, int batch, cudaStream_t s) {
 
 template <typename R>
 cudaError_t dispatch(const JacobiArgs &a, int Mcap, int batch, cudaStream_t s) {
-  if (Mcap <= 64) return run<R, 32, 2>(a, batch, s);
-  if (Mcap <= 128) return run<R, 32, 4>(a, batch, s);
+  if (Mcap <= 64) return run<R, 32, 2, 512, 1, true>(a, batch, s);
+  if (Mcap <= 128) return run<R, 32, 4, 512, 1, true>(a, batch, s);
   if constexpr (sizeof(R) == 4)  // 16-column blocks, 8 warps, two CTAs per SM
     if (Mcap <= 256) return run<R, 16, 8, 256, 2, true>(a, batch, s);
-  if (Mcap <= 256) return run<R, sizeof(R) == 8 ? 16 : 32, 8>(a, batch, s);
-  return run<R, sizeof(R) == 8 ? 8 : 16, 16>(a, batch, s);
+  if (Mcap <= 256) return run<R, sizeof(R) == 8 ? 16 : 32, 8, 512, 1, true>(a, batch, s);
+  return run<R, sizeof(R) == 8 ? 8 : 16, 16, sizeof(R) == 8 ? 256 : 512, 1, true>(a, batch, s);
 }
 
 }  // namespace
