@@ -41,7 +41,6 @@ FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 N_SMS = 152
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (nominal)
 
-
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -308,6 +307,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(device)
 
     def step(ev=None):
+        if ev is not None:  # timed steps sit in an NVTX range (launch lists filter on it)
+            torch.cuda.nvtx.range_push("bench_step")
         m.reset()
         if ev is not None:
             ev[0].record(stream)
@@ -317,6 +318,7 @@ def run_gpu(args):
         m.expect_dev(ps, energy)
         if ev is not None:
             ev[2].record(stream)
+            torch.cuda.nvtx.range_pop()
 
     for _ in range(args.warmup):
         step()

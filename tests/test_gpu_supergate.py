@@ -166,3 +166,27 @@ def test_bad_arguments():
         m.apply_supergate(tnmps.Supergate(10, BLOCK, BLOCK_THETA), chi_max=4)
     with pytest.raises(tnmps.TnmpsError):
         m.apply_supergate(tnmps.Supergate(8, BLOCK, BLOCK_THETA), chi_max=9)
+
+
+def test_chi128_window_matches_oracle():
+    # full size: the chi = 128 benchmark states (40 qubits, 10 layers) and the
+    # measured six-qubit block; the oracle fits the first two states
+    wl = inputs.workload("chi128")
+    B = 2
+    th = wl["thetas"][:B]
+    m = tnmps.MPSBatch(40, 128, B, dtype="c64_bf16split", max_params=wl["n_params"],
+                       eps=wl["eps"])
+    m.apply_circuit(wl["circuit"], th)
+    block, bth = inputs.supergate_block(17, inputs.rng_for(5, 11))
+    kw = dict(chi_max=128, target=1e-10, tol=-1.0, max_sweeps=2)
+    F, F0, info = m.apply_supergate(tnmps.Supergate(40, block, bth), **kw)
+    assert info == {"sweeps": 2, "stages": 1, "chi": 128}
+    terms = [(1.0, [19], [3]), (0.5, [18, 21], [1, 1]), (-0.7, [17, 22], [2, 3])]
+    _, pt = m.expect(tnmps.PauliSum(40, terms), per_term=True)
+    for b in range(B):
+        om = OM.MPS(40, 128, wl["eps"]).run(wl["circuit"], th[b])
+        phi, f, _, _, f0 = OSG.apply_supergate(om, block, bth, **kw)
+        assert abs(F0[b] - f0) <= 1e-5 and abs(F[b] - f) <= 1e-5
+        assert F[b] > F0[b] + 0.05
+        for k, (_, sites, paulis) in enumerate(terms):
+            assert abs(pt[b, k] - phi.expect_pauli(sites, paulis).real) <= 1e-4
