@@ -190,3 +190,32 @@ def test_chi128_window_matches_oracle():
         assert F[b] > F0[b] + 0.05
         for k, (_, sites, paulis) in enumerate(terms):
             assert abs(pt[b, k] - phi.expect_pauli(sites, paulis).real) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_window_at_the_last_site_then_circuit(dtype):
+    # window reaching site n-1, a second super-gate, then an ordinary circuit and
+    # the energy: the context's gauge and bond bookkeeping after a fit must hold
+    n, B = 9, 2
+    m, oms, _, _ = states(n, 3, 16, B, 29, dtype, 1e-10)
+    sg1 = [("CNOT", 8, 5, -1, 0.0, 1.0), ("RY", 6, -1, 0, 0.0, 1.0), ("SWAP", 7, 5, -1, 0.0, 1.0)]
+    sg2 = [("CZ", 1, 4, -1, 0.0, 1.0), ("H", 2, -1, -1, 0.0, 1.0), ("CNOT", 3, 2, -1, 0.0, 1.0)]
+    th = np.array([1.1])
+    kw = dict(target=1e-10, tol=-1.0, max_sweeps=2)
+    F1, _, i1 = m.apply_supergate(tnmps.Supergate(n, sg1, th), chi_max=6, **kw)
+    F2, _, i2 = m.apply_supergate(tnmps.Supergate(n, sg2, None), chi_max=5, **kw)
+    tail = [("RX", q, -1, -1, 0.3 * (q + 1), 1.0) for q in range(n)] + \
+           [("CNOT", q, q + 1, -1, 0.0, 1.0) for q in range(n - 1)]
+    m.apply_circuit(tail)
+    terms = [(1.0, [0], [3]), (0.4, [4, 5], [1, 2]), (-0.6, [7, 8], [3, 3]), (0.2, [2, 6], [2, 1])]
+    e, pt = m.expect(tnmps.PauliSum(n, terms), per_term=True)
+    tol = FTOL[dtype]
+    for b in range(B):
+        p1, f1, _, _, _ = OSG.apply_supergate(oms[b], sg1, th, chi_max=6, **kw)
+        p2, f2, _, _, _ = OSG.apply_supergate(p1, sg2, None, chi_max=5, **kw)
+        assert abs(F1[b] - f1) <= tol and abs(F2[b] - f2) <= tol
+        p2.chi_max = 16
+        p2.run(tail, None)
+        ref = np.array([p2.expect_pauli(s, p).real for _, s, p in terms])
+        assert np.max(np.abs(pt[b] - ref)) <= (1e-9 if dtype == "c128" else 2e-5)
+    assert i1["chi"] == 6 and i2["chi"] == 5
