@@ -1066,7 +1066,8 @@ tnmps_status tnmps_apply_supergate(tnmps_ctx *c, const tnmps_supergate *sg, int 
     return TNMPS_OK;
   }
   const FitLayout L = fit_layout(c, sg);
-  if (!ws) return fail(c, TNMPS_ERR_ARG, "null workspace");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(c, TNMPS_ERR_ARG, "workspace null or not 256-byte aligned");
   if (ws_bytes < L.total) return fail(c, TNMPS_ERR_NOMEM, "super-gate workspace too small");
   if ((st = move_centre(c, p)) != TNMPS_OK) return st;
   char *w8 = static_cast<char *>(ws);
@@ -1145,7 +1146,10 @@ tnmps_status tnmps_apply_supergate(tnmps_ctx *c, const tnmps_supergate *sg, int 
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->dims, w8 + L.pdims, 4 * (size_t)B * (c->n + 1),
                             cudaMemcpyDeviceToDevice, c->stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "super-gate restore");
+      if (e != cudaSuccess) {
+        c->fit_cap = 0;
+        return cuda_fail(c, e, "super-gate restore");
+      }
       c->ub = ub0;
       c->centre = p;
     }
