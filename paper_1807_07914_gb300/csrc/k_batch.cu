@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *S0 = reinterpret_cast<cx<R> *>(smraw);
   cx<R> *S1 = S0 + BC * 256;
+  // third Jacobi staging slot (next block copied ahead) where it fits beside the
+  // kernel's static shared memory: 16-column blocks only
+  cx<R> *S2 = BC == 16 ? S1 + BC * 256 : nullptr;
   __shared__ int64_t s_off[BATCH_MAX_N + 1];
   __shared__ int64_t s_roff[BATCH_MAX_N + 1];
   __shared__ int s_dims[BATCH_MAX_N + 1];
@@ -228,7 +231,8 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
         bool conv;
         int rot, chk;
         // 8 warps: with 16-column blocks each warp keeps its two x columns in registers
-        jac::jacobi_run<R, BC, 8, BC == 16>(W, M, N, M, S0, S1, 1.0f, 30, &conv, &rot, &chk);
+        jac::jacobi_run<R, BC, 8, BC == 16, BC == 16>(W, M, N, M, S0, S1, 1.0f, 30, &conv, &rot,
+                                                      &chk, S2);
         if (!conv && N > 1) {
           if (tid == 0) atomicOr(a.err, TNMPS_EFLAG_NOT_CONVERGED);
         }
@@ -698,7 +702,7 @@ tnmps_status tnmps_batch_bind(tnmps_batch *b, void *arena, size_t bytes, int cta
 static cudaError_t enqueue(tnmps_batch *b) {
   cudaError_t e = cudaMemsetAsync(b->args.counter, 0, 4, b->stream);
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)2 * b->bc * 256 * sizeof(cx<float>);
+  const size_t smem = (size_t)(b->bc == 16 ? 3 : 2) * b->bc * 256 * sizeof(cx<float>);
   if (b->bc == 32) {
     e = cudaFuncSetAttribute(k_batch<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_batch<32><<<b->grid, 256, smem, b->stream>>>(b->args);
@@ -722,7 +726,7 @@ tnmps_status tnmps_batch_capture_graph(tnmps_batch *b) {
     b->graph = nullptr;
   }
   // attributes are set outside the capture
-  const size_t smem = (size_t)2 * b->bc * 256 * sizeof(cx<float>);
+  const size_t smem = (size_t)(b->bc == 16 ? 3 : 2) * b->bc * 256 * sizeof(cx<float>);
   cudaError_t e = b->bc == 32 ? cudaFuncSetAttribute(k_batch<32>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)smem)
