@@ -211,6 +211,234 @@ __device__ void householder_qr(cx<R> *W, int m, int n, cx<R> *tau, R *red, cx<R>
 }
 
 // Q = H_0 ... H_{r-1} [I; 0] (m x r, column-major ld m) from the reflectors in W.
+// ------------------------------------------------ blocked (compact WY) form
+// The reflectors j0..j0+nb-1 of a panel combine into H_j0 ... H_{j0+nb-1} =
+// I - V T V^H (T upper triangular, nb x nb; column k of V is v_{j0+k}: 1 on
+// row j0+k, W below it, 0 above). Applying a panel's block reflector reads each
+// target column once per panel instead of once per reflector.
+
+// v_{j0+k}[i] from the factored W (ld ldw)
+template <typename R>
+__device__ __forceinline__ cx<R> vrow(const cx<R> *W, int ldw, int j0, int k, int i) {
+  const int d = j0 + k;
+  return i > d ? W[(int64_t)d * ldw + i] : mkc<R>(i == d ? R(1) : R(0), R(0));
+}
+
+// Sum K per-lane values over the warp; every lane receives all K sums
+// (halving exchanges, then a broadcast from the lane that holds each sum).
+template <typename R, int K>
+__device__ __forceinline__ void warp_allsum(R *v, int lane) {
+  static_assert(K == 8 || K == 16 || K == 32, "warp_allsum width");
+  R w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = v[k];
+  int n = K;
+#pragma unroll
+  for (int o = 16; o >= 32 / K; o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < K / 2; ++k) {
+      if (k < n / 2) {
+        const R keep = hi ? w[k + n / 2] : w[k];
+        const R send = hi ? w[k] : w[k + n / 2];
+        w[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    n >>= 1;
+  }
+  R t = w[0];
+#pragma unroll
+  for (int o = 16 / K; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = __shfl_sync(0xffffffffu, t, (32 / K) * k);
+}
+
+// Stage the panel's reflectors in shared memory: Vs[k * VLD + (i - j0)] =
+// v_{j0+k}[i] for rows j0 <= i < j0 + VLD (explicit 1 and zeros), k < NB
+// (columns k >= nb zero).
+template <typename R, int NB, int VLD>
+__device__ void stage_panel(const cx<R> *W, int ldw, int j0, int nb, int m, cx<R> *Vs) {
+  for (int e = threadIdx.x; e < NB * VLD; e += blockDim.x) {
+    const int k = e / VLD, i = j0 + (e - k * VLD);
+    Vs[e] = (k < nb && i < m) ? vrow(W, ldw, j0, k, i) : mkc<R>(0, 0);
+  }
+  __syncthreads();
+}
+
+// T of the staged panel into Ts (NB x NB row-major, smem): T[k][k] = tau_k,
+// T[0:k, k] = -tau_k T[0:k, 0:k] (V[:, 0:k]^H v_k). Gs: NB x NB smem scratch.
+template <typename R, int NB, int VLD>
+__device__ void block_tfactor(const cx<R> *Vs, int j0, int nb, int m, const cx<R> *tau, cx<R> *Ts,
+                              cx<R> *Gs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int rows = m - j0 < VLD ? m - j0 : VLD;
+  for (int p = warp; p < nb * nb; p += nw) {
+    const int i = p / nb, k = p - i * nb;
+    if (i >= k) continue;
+    cx<R> acc = mkc<R>(0, 0);
+    for (int row = k + lane; row < rows; row += 32)
+      cfma(acc, cconj(Vs[i * VLD + row]), Vs[k * VLD + row]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) Gs[i * NB + k] = acc;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < NB; ++k) {
+      cx<R> val = mkc<R>(0, 0);
+      if (k < nb && lane < k) {
+        for (int l = lane; l < k; ++l) cfma(val, Ts[lane * NB + l], Gs[l * NB + k]);
+        val = cmul(mkc<R>(-tau[j0 + k].re, -tau[j0 + k].im), val);
+      }
+      __syncwarp();
+      if (lane < NB) {
+        cx<R> out = mkc<R>(0, 0);
+        if (k < nb) out = lane < k ? val : (lane == k ? tau[j0 + k] : mkc<R>(0, 0));
+        Ts[lane * NB + k] = out;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Columns k0..k1-1 of X (ld ldx): x <- (I - V op(T) V^H) x with op(T) = T^H
+// (herm: the QR trailing update, H^H of each reflector in order) or T (forming
+// Q). Only rows >= j0 change. Warp per column, the column in registers
+// (m - j0 <= 32 HR).
+template <typename R, int HR, int NB>
+__device__ void apply_block_reflector(cx<R> *X, int ldx, int k0, int k1, const cx<R> *Vs,
+                                      int j0, int m, const cx<R> *Ts, bool herm) {
+  constexpr int VLD = 32 * HR;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int col = k0 + warp; col < k1; col += nw) {
+    cx<R> *x = X + (int64_t)col * ldx;
+    cx<R> xr[HR];
+    R w[2 * NB];
+#pragma unroll
+    for (int k = 0; k < 2 * NB; ++k) w[k] = R(0);
+#pragma unroll
+    for (int h = 0; h < HR; ++h) {
+      const int i = j0 + lane + 32 * h;
+      xr[h] = i < m ? x[i] : mkc<R>(0, 0);
+      if (i < m) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          const cx<R> v = Vs[k * VLD + lane + 32 * h];
+          w[2 * k] = fma(v.re, xr[h].re, fma(v.im, xr[h].im, w[2 * k]));
+          w[2 * k + 1] = fma(v.re, xr[h].im, fma(-v.im, xr[h].re, w[2 * k + 1]));
+        }
+      }
+    }
+    warp_allsum<R, 2 * NB>(w, lane);
+    // w <- op(T) w in place: T upper (rows ascending), T^H lower (rows descending)
+    if (herm) {
+#pragma unroll
+      for (int i = NB - 1; i >= 0; --i) {
+        cx<R> a = mkc<R>(0, 0);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) cfma(a, cconj(Ts[k * NB + i]), mkc<R>(w[2 * k], w[2 * k + 1]));
+        w[2 * i] = a.re;
+        w[2 * i + 1] = a.im;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        cx<R> a = mkc<R>(0, 0);
+#pragma unroll
+        for (int k = i; k < NB; ++k) cfma(a, Ts[i * NB + k], mkc<R>(w[2 * k], w[2 * k + 1]));
+        w[2 * i] = a.re;
+        w[2 * i + 1] = a.im;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < HR; ++h) {
+      const int i = j0 + lane + 32 * h;
+      if (i < m) {
+        cx<R> a = xr[h];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          const cx<R> v = Vs[k * VLD + lane + 32 * h];
+          a.re -= v.re * w[2 * k] - v.im * w[2 * k + 1];
+          a.im -= v.re * w[2 * k + 1] + v.im * w[2 * k];
+        }
+        x[i] = a;
+      }
+    }
+  }
+}
+
+// householder_qr with panels of NB reflectors: each panel is factored with
+// the reflector-at-a-time loop restricted to its own columns, then its block
+// reflector updates the trailing columns once. Same output as householder_qr.
+template <typename R, int NB, int HR>
+__device__ void householder_qr_blocked(cx<R> *W, int m, int n, cx<R> *tau, R *red, cx<R> *vs,
+                                       cx<R> *Ts, cx<R> *Gs, cx<R> *Vs) {
+  const int r = m < n ? m : n;
+  for (int j0 = 0; j0 < r; j0 += NB) {
+    const int nb = r - j0 < NB ? r - j0 : NB;
+    for (int j = j0; j < j0 + nb; ++j) {
+      cx<R> *col = W + (int64_t)j * m;
+      R part = 0;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
+        part += col[i].re * col[i].re + col[i].im * col[i].im;
+      const R xn2 = block_sum(part, red);
+      const cx<R> alpha = col[j];
+      __syncthreads();
+      cx<R> tj = mkc<R>(0, 0);
+      if (!(xn2 == R(0) && alpha.im == R(0))) {
+        const R beta = -copysign(sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2), alpha.re);
+        tj = mkc<R>((beta - alpha.re) / beta, -alpha.im / beta);
+        const R dr = alpha.re - beta, di = alpha.im;
+        const R den = dr * dr + di * di;
+        const cx<R> sc = mkc<R>(dr / den, -di / den);
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+          const cx<R> v = cmul(col[i], sc);
+          col[i] = v;
+          vs[i] = v;
+        }
+        if (threadIdx.x == 0) {
+          col[j] = mkc<R>(beta, 0);
+          vs[j] = mkc<R>(1, 0);
+        }
+      }
+      if (threadIdx.x == 0) tau[j] = tj;
+      __syncthreads();
+      if ((tj.re == R(0) && tj.im == R(0)) || j + 1 >= j0 + nb) continue;
+      if (m <= 256) reflect_columns<R, 8>(W, m, j + 1, j0 + nb, j, m, vs, cconj(tj));
+      else reflect_columns<R, 16>(W, m, j + 1, j0 + nb, j, m, vs, cconj(tj));
+      __syncthreads();
+    }
+    if (j0 + nb >= n) continue;
+    stage_panel<R, NB, 32 * HR>(W, m, j0, nb, m, Vs);
+    block_tfactor<R, NB, 32 * HR>(Vs, j0, nb, m, tau, Ts, Gs);
+    apply_block_reflector<R, HR, NB>(W, m, j0 + nb, n, Vs, j0, m, Ts, true);
+    __syncthreads();
+  }
+}
+
+// householder_form_q with the block reflectors of NB-wide panels, last panel first.
+template <typename R, int NB, int HR>
+__device__ void householder_form_q_blocked(const cx<R> *W, int m, int n, const cx<R> *tau,
+                                           cx<R> *Q, cx<R> *Ts, cx<R> *Gs, cx<R> *Vs) {
+  const int r = m < n ? m : n;
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int q = e / m, i = e - q * m;
+    Q[e] = mkc<R>(i == q ? R(1) : R(0), 0);
+  }
+  __syncthreads();
+  for (int j0 = ((r - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
+    const int nb = r - j0 < NB ? r - j0 : NB;
+    stage_panel<R, NB, 32 * HR>(W, m, j0, nb, m, Vs);
+    block_tfactor<R, NB, 32 * HR>(Vs, j0, nb, m, tau, Ts, Gs);
+    apply_block_reflector<R, HR, NB>(Q, m, j0, r, Vs, j0, m, Ts, false);
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *tau, cx<R> *Q,
                                    cx<R> *vs) {
@@ -235,8 +463,11 @@ __device__ void householder_form_q(const cx<R> *W, int m, int n, const cx<R> *ta
 
 // Right move core: C (2Dl x Dr row-major, in X) = Q R. X <- Q (Dl, 2, r);
 // R stays in the upper triangle of W (column-major, ld 2Dl); Qbuf scratch.
-// Returns r = min(2Dl, Dr). Whole CTA.
-template <typename R>
+// Returns r = min(2Dl, Dr). Whole CTA. HR > 0: panels of NB reflectors staged
+// in shared memory and applied as block reflectors, 2 Dl <= 32 HR (one
+// reflector at a time when the staged panel does not fit the static shared
+// memory: complex128 with HR = 16); HR = 0: one reflector at a time.
+template <typename R, int HR = 0, int NB = sizeof(R) == 4 ? 8 : 4>
 __device__ int qr_right_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
   const int m = 2 * Dl, n = Dr, r = m < n ? m : n;
   __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
@@ -248,8 +479,17 @@ __device__ int qr_right_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
     W[e] = X[(int64_t)i * n + k];
   }
   __syncthreads();
-  householder_qr(W, m, n, tau, red, vs);
-  householder_form_q(W, m, n, tau, Qbuf, vs);
+  // staged panel + tau/vs arrays within 40 KB of static shared memory
+  if constexpr (HR > 0 &&
+                (NB * 32 * HR + 4 * TNMPS_MAX_CHI) * sizeof(cx<R>) <= 40960) {
+    __shared__ cx<R> Ts[NB * NB], Gs[NB * NB];
+    __shared__ __align__(16) cx<R> Vs[NB * 32 * HR];  // the panel's reflectors
+    householder_qr_blocked<R, NB, HR>(W, m, n, tau, red, vs, Ts, Gs, Vs);
+    householder_form_q_blocked<R, NB, HR>(W, m, n, tau, Qbuf, Ts, Gs, Vs);
+  } else {
+    householder_qr(W, m, n, tau, red, vs);
+    householder_form_q(W, m, n, tau, Qbuf, vs);
+  }
   for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
     const int i = e / r, q = e - i * r;
     X[e] = Qbuf[(int64_t)q * m + i];
@@ -260,8 +500,8 @@ __device__ int qr_right_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
 
 // Left move core: C (Dl x 2Dr row-major, in X) = L Q via QR of C^H = Q' R'.
 // X <- Q'^H (r, 2, Dr); R' stays in W (column-major, ld 2Dr), L = R'^H.
-// Returns r = min(2Dr, Dl). Whole CTA.
-template <typename R>
+// Returns r = min(2Dr, Dl). Whole CTA. HR as in qr_right_cta (2 Dr <= 32 HR).
+template <typename R, int HR = 0, int NB = sizeof(R) == 4 ? 8 : 4>
 __device__ int lq_left_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
   const int m = 2 * Dr, n = Dl, r = m < n ? m : n;
   __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
@@ -270,8 +510,17 @@ __device__ int lq_left_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
   __syncthreads();
   for (int e = threadIdx.x; e < m * n; e += blockDim.x) W[e] = cconj(X[e]);
   __syncthreads();
-  householder_qr(W, m, n, tau, red, vs);
-  householder_form_q(W, m, n, tau, Qbuf, vs);
+  // staged panel + tau/vs arrays within 40 KB of static shared memory
+  if constexpr (HR > 0 &&
+                (NB * 32 * HR + 4 * TNMPS_MAX_CHI) * sizeof(cx<R>) <= 40960) {
+    __shared__ cx<R> Ts[NB * NB], Gs[NB * NB];
+    __shared__ __align__(16) cx<R> Vs[NB * 32 * HR];  // the panel's reflectors
+    householder_qr_blocked<R, NB, HR>(W, m, n, tau, red, vs, Ts, Gs, Vs);
+    householder_form_q_blocked<R, NB, HR>(W, m, n, tau, Qbuf, Ts, Gs, Vs);
+  } else {
+    householder_qr(W, m, n, tau, red, vs);
+    householder_form_q(W, m, n, tau, Qbuf, vs);
+  }
   for (int e = threadIdx.x; e < r * m; e += blockDim.x) X[e] = cconj(Qbuf[e]);
   __syncthreads();
   return r;

@@ -299,22 +299,22 @@ __global__ void __launch_bounds__(256) k_gate1(StateView v, Op1 op, const double
 
 // ---------------------------------------------------------------- K7
 // Right move at site c: C_c (2Dl x Dr) = Q R;  A_c <- Q;  R stays in w_buf.
-template <typename R>
+template <typename R, int HR>
 __global__ void __launch_bounds__(256) k_qr_right(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
                                                   int64_t tw, int32_t *newdim) {
   const int b = blockIdx.x;
-  const int r = gdev::qr_right_cta<R>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
+  const int r = gdev::qr_right_cta<R, HR>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
                                       wbuf + (int64_t)b * tw, tbuf + (int64_t)b * tw);
   if (threadIdx.x == 0) newdim[b] = r;
 }
 
 // Left move at site c: C_c (Dl x 2Dr) = L Q via QR of C_c^H = Q' R';
 // B_c <- Q'^H,  L = R'^H stays (as R') in w_buf.
-template <typename R>
+template <typename R, int HR>
 __global__ void __launch_bounds__(256) k_lq_left(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
                                                  int64_t tw, int32_t *newdim) {
   const int b = blockIdx.x;
-  const int r = gdev::lq_left_cta<R>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
+  const int r = gdev::lq_left_cta<R, HR>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
                                      wbuf + (int64_t)b * tw, tbuf + (int64_t)b * tw);
   if (threadIdx.x == 0) newdim[b] = r;
 }
@@ -515,7 +515,11 @@ cudaError_t move_right_impl(tnmps_ctx *c, int s) {
   cx<R> *tb = reinterpret_cast<cx<R> *>(c->theta_buf);
   cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
   cudaEvent_t ev = prof_begin(c, PC_MOVE);
-  k_qr_right<R><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
+  // block reflectors hold a column's rows in registers: 8 per lane up to 256 rows
+  if (2 * c->chi <= 256)
+    k_qr_right<R, 8><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
+  else
+    k_qr_right<R, 16><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
   c->launches += 4;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -545,7 +549,10 @@ cudaError_t move_left_impl(tnmps_ctx *c, int s) {
   cx<R> *tb = reinterpret_cast<cx<R> *>(c->theta_buf);
   cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
   cudaEvent_t ev = prof_begin(c, PC_MOVE);
-  k_lq_left<R><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
+  if (2 * c->chi <= 256)
+    k_lq_left<R, 8><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
+  else
+    k_lq_left<R, 16><<<c->batch, 256, 0, c->stream>>>(v, s, wb, tb, c->tw, c->perm);
   c->launches += 4;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
