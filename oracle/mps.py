@@ -11,7 +11,7 @@ Paper passages followed (arXiv:1807.07914):
   singular values below a cutoff epsilon truncated (default 1e-4).
 * Sec. II, Fig. "mpssvd": accelerated update of adjacent qubit pairs.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 
 * Cutoff rule R: with sigma sorted descending and sigma_norm = sqrt(sum
   sigma^2), keep sigma_i >= eps * sigma_norm, then cap at chi_max keeping

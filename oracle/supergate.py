@@ -14,7 +14,7 @@ the input network TN_inp by
   (6) while the value reached is not acceptable, enlarging the auxiliary
       (bond) dimensions of TN_out and repeating (5).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 
 * TN_mid's gates form a matrix-product operator W over the window [p, q] of
   qubits the super-gate touches (the identity elsewhere). W[i] has shape

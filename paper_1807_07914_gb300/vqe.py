@@ -15,7 +15,7 @@ for a sweep of parameter values. Here an optimiser drives the parameters:
   its MPS energy is lower. Every MPS-evaluated point (proposals and the 2P
   parameter-shift points) joins the surrogate's training data, and the
   surrogate is fine-tuned on recent points. The MPS is therefore both the
-  fallback and the judge: the reported energies are all MPS energies.
+  fallback and the arbiter: the reported energies are all MPS energies.
 """
 import json
 import time
@@ -241,8 +241,8 @@ def main():
     theta0 = rng.uniform(-np.pi, np.pi, P)
     plain = MPSEnergy(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"], "c128", 641)
     hp, bp = plain_adam(plain, theta0, a.lr, a.budget)
-    judge = MPSEnergy(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"], "c128", 641)
-    hs, bs, st = surrogate_adam(judge, sur, theta0, a.lr, a.budget)
+    verifier = MPSEnergy(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"], "c128", 641)
+    hs, bs, st = surrogate_adam(verifier, sur, theta0, a.lr, a.budget)
     e_star = min(bp[0], bs[0])
     target = e_star + 1e-4
     out = {"workload": "heis40: n=40, 4 layers Ry/Rz + CNOT ladder (320 params), chi 64, "

@@ -42,8 +42,8 @@ def test_surrogate_reaches_plain_best_with_fewer_evaluations():
     budget = 20000
     plain = vqe.MPSEnergy(n, 16, 1e-12, circ, P, terms, "c128", 2 * P + 1)
     hp, bp = vqe.plain_adam(plain, theta0, 0.05, budget)
-    judge = vqe.MPSEnergy(n, 16, 1e-12, circ, P, terms, "c128", 2 * P + 1)
-    hs, bs, st = vqe.surrogate_adam(judge, sur, theta0, 0.05, budget)
+    verifier = vqe.MPSEnergy(n, 16, 1e-12, circ, P, terms, "c128", 2 * P + 1)
+    hs, bs, st = vqe.surrogate_adam(verifier, sur, theta0, 0.05, budget)
     # every reported energy is an MPS energy; the surrogate run is monotone
     assert all(b[1] <= a[1] for a, b in zip(hs, hs[1:]))
     assert st["accepted"] > 0
