@@ -494,13 +494,17 @@ cudaError_t split_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
     ++c->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  ProbSplit<R> ps{};
-  ps.v = v;
-  ps.l = l;
-  ps.tb = tb;
-  ps.tw = c->tw;
-  if ((e = launch_gemm<R>(ps, kub, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
-    return e;
+  if (c->dtype == TNMPS_C64_BF16SPLIT) {  // tensor cores, three BF16 pieces
+    if ((e = launch_split_tc(c, l, kub)) != cudaSuccess) return e;
+  } else {
+    ProbSplit<R> ps{};
+    ps.v = v;
+    ps.l = l;
+    ps.tb = tb;
+    ps.tw = c->tw;
+    if ((e = launch_gemm<R>(ps, kub, Nmax, c->batch, c->stream, &c->launches)) != cudaSuccess)
+      return e;
+  }
   k_normalise_site<R><<<c->batch, 256, 0, c->stream>>>(v, l + 1);
   ++c->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

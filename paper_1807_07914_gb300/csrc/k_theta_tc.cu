@@ -44,6 +44,7 @@ struct ThetaArgs {
   int64_t a_stride, b_stride;
   float *theta;  // theta_buf as interleaved complex64
   int64_t tw;
+  const cx<float> *theta_in;  // theta_buf as the split's B operand source
 };
 
 __device__ __forceinline__ int dimb(const ThetaArgs &t, int b, int i) {
@@ -155,10 +156,141 @@ struct ThetaProb {
   __device__ void done(const Unit &) const {}
 };
 
+// ---------------------------------------------------------------- K4 split
+// C_{l+1} = U_k^H Theta (k x 2Dr), the right factor of the split, as the same
+// split-precision C = A B^T with
+//     A = U_k^H as rows kappa < k along K = (a,s1) < 2Dl (U_k: site l, ld k)
+//     B = rows (s2,c) < 2Dr along K = (a,s1)           (Theta: theta_buf)
+// and the FP32 result written into site l+1 (ld 2Dr). Three pieces, as K2:
+// C_{l+1} is the next centre of the state.
+__host__ __device__ inline int sa_tiles(int chi) { return (chi + 63) / 64; }
+__host__ __device__ inline int sk_chunks(int chi) { return (2 * chi + 31) / 32; }
+
+__global__ void __launch_bounds__(256) k_split_prep(ThetaArgs t) {
+  const int b = blockIdx.y;
+  const int Dl = dimb(t, b, t.l), k = dimb(t, b, t.l + 1), Dr = dimb(t, b, t.l + 2);
+  const int M2 = 2 * Dl, N2 = 2 * Dr;
+  const int MT = dcdiv(k, 64), Kc = dcdiv(M2, KCH);
+  const int RT = dcdiv(round32(N2), 128);
+  const int mtc = sa_tiles(t.chi), rtc = b_tiles(t.chi);
+  const cx<float> *U = t.sites + (int64_t)b * t.state_elems + t.site_off[t.l];
+  const cx<float> *Th = t.theta_in + (int64_t)b * t.tw;
+  uint8_t *A = t.A + (int64_t)b * t.a_stride;
+  uint8_t *B = t.B + (int64_t)b * t.b_stride;
+  const int64_t na = (int64_t)MT * Kc * 1024, nbv = (int64_t)RT * Kc * 1024;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + nbv;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const bool isA = e < na;
+    const int64_t f = isA ? e : e - na;
+    const int r = (int)(f & 127), kv = (int)((f >> 7) & 7);
+    const int64_t rest = f >> 10;
+    const int q = (int)(rest % Kc), tile = (int)(rest / Kc);
+    const int half = kv >> 2;
+    const int m0 = q * KCH + (kv & 3) * 8;
+    float v[8];
+    if (isA) {  // conj(U[i][kappa]) along K = i
+      const int part = r >> 6, kap = tile * 64 + (r & 63);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = m0 + u;
+        cx<float> x = (kap < k && i < M2) ? U[(int64_t)i * k + kap] : mkc<float>(0.f, 0.f);
+        x.im = -x.im;
+        v[u] = part == 0 ? (half == 0 ? x.re : -x.im) : (half == 0 ? x.im : x.re);
+      }
+      store_pieces8<PC>(A + ((int64_t)(q * PC) * mtc + tile) * TILE, (int64_t)mtc * TILE, r, kv, v,
+                        1.f);
+    } else {  // Theta[i][j] along K = i
+      const int j = tile * 128 + r;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = m0 + u;
+        const cx<float> x = (j < N2 && i < M2) ? Th[(int64_t)i * N2 + j] : mkc<float>(0.f, 0.f);
+        v[u] = half == 0 ? x.re : x.im;
+      }
+      store_pieces8<PC>(B + ((int64_t)(q * PC) * rtc + tile) * TILE, (int64_t)rtc * TILE, r, kv, v,
+                        1.f);
+    }
+  }
+}
+
+template <int NMAX>
+struct SplitProb : ThetaProb<NMAX> {
+  __device__ bool setup(int item, Unit &u) const {
+    const ThetaArgs &t = this->t;
+    const int per = this->grid_m * this->grid_n;
+    const int b = item / per, rest = item - b * per;
+    const int g = rest / this->grid_n, nt = rest - g * this->grid_n;
+    const int Dl = dimb(t, b, t.l), k = dimb(t, b, t.l + 1), Dr = dimb(t, b, t.l + 2);
+    if (g >= dcdiv(k, 64)) return false;
+    const int npad = round32(2 * Dr);
+    if (nt * NMAX >= npad) return false;
+    const int mtc = sa_tiles(t.chi), rtc = b_tiles(t.chi);
+    u.a = t.A + (int64_t)b * t.a_stride + (int64_t)g * TILE;
+    u.a_pc = (int64_t)mtc * TILE;
+    u.a_kt = PC * u.a_pc;
+    u.a_s = 0;
+    u.b = t.B + (int64_t)b * t.b_stride + (int64_t)(nt * (NMAX / 128)) * TILE;
+    u.b_pc = (int64_t)rtc * TILE;
+    u.b_kt = PC * u.b_pc;
+    u.b_s = 0;
+    u.kc = u.nk = dcdiv(2 * Dl, KCH);
+    u.N = min(NMAX, npad - nt * NMAX);
+    u.b_bytes = (uint32_t)u.N * 128u;
+    u.out = reinterpret_cast<uint8_t *>(
+        const_cast<cx<float> *>(t.sites + (int64_t)b * t.state_elems + t.site_off[t.l + 1]));
+    u.row0 = g * 64;
+    u.col0 = nt * NMAX;
+    u.rows = k;
+    u.cols = 2 * Dr;
+    u.flops = 0;
+    return true;
+  }
+};
+
 }  // namespace
 
-int64_t theta_tc_a_bytes(int chi) { return (int64_t)k_chunks(chi) * PC * a_tiles(chi) * TILE; }
-int64_t theta_tc_b_bytes(int chi) { return (int64_t)k_chunks(chi) * PC * b_tiles(chi) * TILE; }
+// operand bytes per state: the larger of K2 (A: 2chi rows, K = chi) and the
+// split (A: chi rows, K = 2chi; B: K = 2chi)
+int64_t theta_tc_a_bytes(int chi) {
+  const int64_t k2 = (int64_t)k_chunks(chi) * PC * a_tiles(chi) * TILE;
+  const int64_t sp = (int64_t)sk_chunks(chi) * PC * sa_tiles(chi) * TILE;
+  return k2 > sp ? k2 : sp;
+}
+int64_t theta_tc_b_bytes(int chi) {
+  const int64_t k2 = (int64_t)k_chunks(chi) * PC * b_tiles(chi) * TILE;
+  const int64_t sp = (int64_t)sk_chunks(chi) * PC * b_tiles(chi) * TILE;
+  return k2 > sp ? k2 : sp;
+}
+
+cudaError_t launch_split_tc(tnmps_ctx *c, int l, int kub) {
+  ThetaArgs t{};
+  t.sites = reinterpret_cast<const cx<float> *>(c->sites);
+  t.site_off = c->site_off_dev;
+  t.dims = c->dims;
+  t.state_elems = c->state_elems;
+  t.n = c->n;
+  t.l = l;
+  t.chi = c->chi;
+  t.A = reinterpret_cast<uint8_t *>(c->tc_a);
+  t.B = reinterpret_cast<uint8_t *>(c->tc_b);
+  t.a_stride = c->tc_a_stride;
+  t.b_stride = c->tc_b_stride;
+  t.theta_in = reinterpret_cast<const cx<float> *>(c->theta_buf);
+  t.tw = c->tw;
+  k_split_prep<<<dim3(8, c->batch), 256, 0, c->stream>>>(t);
+  ++c->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int gm = (kub + 63) / 64;
+  const int npad = (2 * c->ub[l + 2] + 31) & ~31;
+  const int gn = (npad + 127) / 128;
+  SplitProb<128> p{};
+  p.t = t;
+  p.grid_m = gm;
+  p.grid_n = gn;
+  return ctc::launch_cgemm<SplitProb<128>, 128>(p, (int64_t)c->batch * gm * gn, c->err, c->stream,
+                                                &c->launches);
+}
 
 cudaError_t launch_theta_tc(tnmps_ctx *c, int l) {
   ThetaArgs t{};

@@ -231,6 +231,9 @@ cudaError_t launch_sample(tnmps_ctx *c, const double *u, int shots, uint8_t *bit
 cudaError_t launch_theta_tc(tnmps_ctx *c, int l);
 int64_t theta_tc_a_bytes(int chi);
 int64_t theta_tc_b_bytes(int chi);
+// K4 of the BF16-split form: C_{l+1} = U_k^H Theta on the tensor cores into site
+// l+1 (U_k in site l, Theta in theta_buf, k = dims[l+1] <= kub)
+cudaError_t launch_split_tc(tnmps_ctx *c, int l, int kub);
 cudaError_t launch_jacobi_standalone(tnmps_dtype dt, int batch, int m, int n, void *a, int lda,
                                      double *sigma, int32_t *sweeps, int max_sweeps,
                                      cudaStream_t s);
