@@ -59,13 +59,17 @@ typedef struct tnmps_supergate tnmps_supergate;
 /* Arithmetic of the state and of the contractions. TNMPS_C128: complex128
  * everywhere (the plain FP64 form). TNMPS_C64: complex64 storage and FP32
  * contractions/rotations; the energy reduction stays FP64.
- * TNMPS_C64_BF16SPLIT: as TNMPS_C64, except that the transfer-matrix sweeps
- * of the expectation values run on the tensor cores as split-precision
- * complex products: every FP32 operand value is split into two BF16 values
- * hi + lo and each real product is hi*hi + hi*lo + lo*hi, accumulated in
- * FP32 (relative rounding of order 2^-16 per product). Its state arena and
- * circuit calls are those of TNMPS_C64; only the expectation workspace
- * differs. */
+ * TNMPS_C64_BF16SPLIT: as TNMPS_C64, except that three contractions run on
+ * the tensor cores as split-precision complex products, accumulated in FP32:
+ *   - the transfer-matrix sweeps of the expectation values, with every FP32
+ *     operand value split into two BF16 values hi + lo and each real product
+ *     formed as hi*hi + hi*lo + lo*hi (relative rounding of order 2^-16);
+ *   - the two-site block of a gate and the right factor U_k^H Theta of its
+ *     split, with three BF16 pieces per value (the whole FP32 mantissa, six
+ *     piece products), since both feed the state itself.
+ * The Jacobi SVD and the orthonormalisation step are those of TNMPS_C64. The
+ * state arena holds the converted operands of the tensor-core gate products
+ * in addition (tnmps_state_bytes accounts for them). */
 typedef enum { TNMPS_C128 = 0, TNMPS_C64 = 1, TNMPS_C64_BF16SPLIT = 2 } tnmps_dtype;
 
 typedef enum {
