@@ -219,3 +219,17 @@ def test_window_at_the_last_site_then_circuit(dtype):
         ref = np.array([p2.expect_pauli(s, p).real for _, s, p in terms])
         assert np.max(np.abs(pt[b] - ref)) <= (1e-9 if dtype == "c128" else 2e-5)
     assert i1["chi"] == 6 and i2["chi"] == 5
+
+
+def test_one_qubit_window_applies_exactly():
+    n = 6
+    m, oms, circ, th = states(n, 2, 8, 2, 31, "c128", 1e-12)
+    gates = [("RY", 3, -1, 0, 0.0, 1.0), ("H", 3, -1, -1, 0.0, 1.0)]
+    F, F0, info = m.apply_supergate(tnmps.Supergate(n, gates, np.array([0.4])), chi_max=8)
+    assert np.all(F == 1.0) and info["sweeps"] == 0
+    for b in range(2):
+        psi = SV.run_circuit(n, circ, th[b])
+        psi = SV.apply_1q(psi, n, G.ry(0.4), 3)
+        psi = SV.apply_1q(psi, n, G.H, 3)
+        v = dense(gpu_sites(m, b))
+        assert abs(abs(np.vdot(v, psi)) - 1.0) <= 1e-10

@@ -97,3 +97,13 @@ def test_bad_gates_rejected(T):
         T.Supergate(4, [("RY", 1, -1, 2, 0.0, 1.0)], np.zeros(2))  # parameter index
     with pytest.raises(T.TnmpsError):
         T.Supergate(4, [("CZ", 2, 2, -1, 0.0, 1.0)])          # same qubit twice
+
+
+def test_empty_and_one_qubit_super_gates(T):
+    with pytest.raises(T.TnmpsError):
+        T.Supergate(4, [])
+    sg = T.Supergate(6, [("RY", 3, -1, 0, 0.0, 1.0), ("H", 3, -1, -1, 0.0, 1.0)], np.array([0.4]))
+    assert (sg.first, sg.last) == (3, 3) and list(sg.bonds) == [1, 1]
+    W = sg.mpo()
+    U = G.H @ G.ry(0.4)
+    np.testing.assert_allclose(W[0][0, :, :, 0], U, atol=1e-14)
