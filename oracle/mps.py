@@ -30,7 +30,9 @@ Readings where the paper is silent:
 Pins: ``tests/test_oracle_mps.py`` -- agreement with the dense brute force
 when nothing is truncated, norm 1 after every gate, the truncation error of
 one step equal to its discarded weight, GHZ and product-state closed forms at
-n=40, bond-dimension bounds, and the cutoff semantics.
+n=40, bond-dimension bounds, and the cutoff semantics; ``cut_margin`` against
+closed forms (a two-value Schmidt spectrum at the cutoff, a planted gap at the
+cap, the exact tie of a Bell pair cut to one value).
 """
 import numpy as np
 
@@ -49,6 +51,25 @@ def truncation_rank(sigma, chi_max, eps):
     return k, w, float(np.sqrt(np.sum(s2[:k])))
 
 
+def cut_margin(sigma, chi_max, eps):
+    """How far one step's truncation decision is from changing, relative to
+    sigma_0. Returns (d_cut, d_cap): d_cut is the smallest distance of any
+    sigma_i from the cutoff eps * sigma_norm (a perturbation of the sigma
+    below it keeps the same count above the cutoff); d_cap, when the chi_max
+    cap binds, is the gap sigma_{k-1} - sigma_k between the last kept and the
+    first dropped value (below it the kept subspace is not unique: a tie at
+    the cut), else inf. Diagnostic only: no part of the simulation uses it.
+    ``sigma`` sorted descending."""
+    s = np.asarray(sigma, dtype=np.float64)
+    if s.size == 0 or not s[0] > 0:
+        return float("inf"), float("inf")
+    norm = np.sqrt(float(np.sum(s ** 2)))
+    d_cut = float(np.min(np.abs(s - eps * norm))) / s[0]
+    keep = int(np.count_nonzero(s >= eps * norm))
+    d_cap = float(s[chi_max - 1] - s[chi_max]) / s[0] if keep > chi_max else float("inf")
+    return d_cut, d_cap
+
+
 class MPS:
     """MPS of n qubits; ``tensors[i]`` has shape (D_{i-1}, 2, D_i)."""
 
@@ -64,6 +85,7 @@ class MPS:
         self.centre = 0
         self.discarded = 0.0          # sum of per-step discarded weights
         self.step_weights = []
+        self.cut_margins = []         # per two-qubit step: (d_cut, d_cap), see cut_margin
 
     # ---- gauge moves -------------------------------------------------
     def _move_right(self):
@@ -111,6 +133,7 @@ class MPS:
         self.centre = l + 1
         self.discarded += w
         self.step_weights.append(w)
+        self.cut_margins.append(cut_margin(S, self.chi_max, self.eps))
 
     def apply_2q(self, G, qa, qb):
         """G (basis 2*s_qa + s_qb) on qubits (qa, qb), any distance."""

@@ -123,6 +123,27 @@ def test_cutoff_is_relative_on_singular_values(s, expected_dim):
         assert abs(m.expect_pauli([0], [3]) - 1.0) < 1e-12
 
 
+def test_cut_margin_closed_forms():
+    """The truncation-decision margins: distance of sigma from the relative
+    cutoff, and the gap at the chi_max cut when the cap binds (both relative
+    to sigma_0)."""
+    a = np.arcsin(5e-5)
+    d_cut, d_cap = M.cut_margin([np.cos(a), np.sin(a)], 8, 1e-4)
+    assert abs(d_cut - 5e-5 / np.cos(a)) < 1e-15 and d_cap == np.inf
+    s = [0.8, 0.4, 0.4 - 1e-9, 0.1]
+    d_cut, d_cap = M.cut_margin(s, 2, 1e-10)                          # cap binds: the gap
+    assert abs(d_cap - 1e-9 / 0.8) < 1e-15
+    assert abs(d_cut - (0.1 - 1e-10 * np.linalg.norm(s)) / 0.8) < 1e-15
+    assert M.cut_margin(s, 4, 1e-10)[1] == np.inf
+    # a Bell pair cut to one value: equal Schmidt values, an exact tie
+    circ = [("H", 0, -1, -1, 0.0, 1.0), ("CNOT", 0, 1, -1, 0.0, 1.0)]
+    m = M.MPS(2, chi_max=1, eps=1e-10).run(circ, [])
+    assert m.cut_margins[-1][1] < 1e-15 and abs(m.discarded - 0.5) < 1e-15
+    m = M.MPS(2, chi_max=2, eps=1e-10).run(circ, [])
+    assert abs(m.cut_margins[-1][0] - (1 - np.sqrt(2) * 1e-10)) < 1e-14
+    assert m.cut_margins[-1][1] == np.inf
+
+
 def test_rounds_circuit_two_rounds_bond_four():
     """Sec. V.A: after two random rounds the maximum bond dimension is 4,
     independent of the register size."""
