@@ -103,9 +103,11 @@ def test_ghz40_long_strings():
     assert np.allclose(pt[0], [1, -1, 1, 0, 1], atol=1e-4)
 
 
-def test_chi128_saturated_states_against_c64():
+def test_chi128_saturated_states_against_oracle_and_c64():
     """Two states of the chi = 128 benchmark workload (middle bonds at 128)
-    with 200 of its random strings and its Heisenberg chain."""
+    with 200 of its random strings and its Heisenberg chain: against the FP64
+    oracle MPS on the same rows, and against the FP32 sweeps on the very same
+    states (which isolates the split-precision sweep)."""
     wl = inputs.workload("chi128")
     th = wl["thetas"][:2]
     terms = wl["terms"] + wl["terms_random"][:200]
@@ -114,12 +116,17 @@ def test_chi128_saturated_states_against_c64():
     _, e64, pt64 = run(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], th, terms, "c64", chunk=1)
     assert np.max(np.abs(pt - pt64)) <= 1e-4
     assert np.max(np.abs(e - e64)) <= 1e-6 * sum_abs(terms)
+    vals, om = OE.term_values_mps(wl["n"], wl["circuit"], th[0], terms, wl["chi_max"], wl["eps"])
+    assert np.array(om.cut_margins)[:, 1].min() > 1e-5      # no tie at the chi_max cut
+    assert np.max(np.abs(pt[0] - vals)) <= 1e-4
+    assert abs(e[0] - OE.energy_from_values(terms, vals)) <= 1e-6 * sum_abs(terms)
 
 
-def test_chi256_bonds_above_128_split_against_c64():
+def test_chi256_bonds_above_128_split_against_oracle():
     """Bonds up to the library's maximum (256): the tensor-core block
     contraction with several 128-wide N tiles and two row tiles, the sweeps'
-    256-wide MMA variant and the 512-row Jacobi, against the FP32 forms."""
+    256-wide MMA variant and the 512-row Jacobi, against the FP64 oracle MPS
+    (the cap binds at 256 in the middle) and against the FP32 forms."""
     n, chi = 18, 256
     circ, P = inputs.hea_circuit(n, 9, ("RY", "RZ"))
     th = inputs.thetas(2, P, np.random.default_rng(256))
@@ -132,3 +139,9 @@ def test_chi256_bonds_above_128_split_against_c64():
     assert np.abs(m.bond_dims().astype(int) - m64.bond_dims()).max() <= 2
     assert np.max(np.abs(pt - pt64)) <= 1e-4
     assert np.max(np.abs(e - e64)) <= 1e-6 * sum_abs(terms)
+    for b in range(2):
+        vals, om = OE.term_values_mps(n, circ, th[b], terms, chi, 1e-10)
+        assert max(om.bond_dims()) == chi
+        assert np.array(om.cut_margins)[:, 1].min() > 1e-5
+        assert np.max(np.abs(pt[b] - vals)) <= 1e-4
+        assert abs(e[b] - OE.energy_from_values(terms, vals)) <= 1e-6 * sum_abs(terms)
