@@ -11,9 +11,14 @@ Prints ONE JSON line. ``value`` = Pauli-term expectations per second
 (whole job: states x terms / step time, the state simulation included);
 ``gates_per_s`` = two-qubit gate applications per second; the dominant
 kernel's roofline (the one-sided Jacobi SVD) is measured live with CUDA
-events on the library's stream. ``random_terms`` reports the metric's second
-term set (2000 random strings of weight <= 4) as one expectation pass over
-the final states, with the tensor-core sweep kernel's roofline.
+events on the library's stream, against the FP32 (or FP64) FMA rate measured
+in the same run by the library's peak kernel (``alu_peaks``).
+``random_terms`` reports the metric's second term set (2000 random strings of
+weight <= 4) as one expectation pass over the final states, with the
+tensor-core sweep kernel's roofline. ``accuracy`` compares the line's energy
+of theta row 0 with the FP64 oracle on the same row (target |dE| <= 1e-6
+sum|c_k|). ``fp64_form`` times one step of the plain FP64 form (complex128
+everywhere) on the same workload, with its own roofline and accuracy.
 
   python bench.py [--gpus N --steps K --warmup W] [--dtype c64_bf16split|c64|c128] [--batch B]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
@@ -37,9 +42,6 @@ from paper_1807_07914_gb300 import inputs  # noqa: E402
 
 METRIC = "Pauli-term expectations/sec and gates/sec at chi=128, 40 qubits; % roofline"
 UNIT = "expectations/s"
-FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
-N_SMS = 152
-FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (nominal)
 
 def load_peaks():
     try:
@@ -142,10 +144,11 @@ def reduce_sum(x, ws, device=None):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(wl, n_theta=1, n_terms=None):
+def oracle_sample(wl, n_theta=1, n_terms=None, energies=None):
     """Time the FP64 oracle (as it stands) on a bounded sample of the same
     workload: the full circuit for n_theta parameter rows and the per-term
-    energy sweeps. Returns (seconds, states, terms_per_state, gates)."""
+    energy sweeps. Returns (seconds, states, terms_per_state, gates); the
+    energies of the rows are appended to ``energies`` when given."""
     from oracle import mps as OM
     terms = wl["terms"] if n_terms is None else wl["terms"][:n_terms]
     t0 = time.perf_counter()
@@ -156,6 +159,8 @@ def oracle_sample(wl, n_theta=1, n_terms=None):
         e = 0.0
         for c, s, p in terms:
             e += c * m.expect_pauli(s, p).real
+        if energies is not None:
+            energies.append(e)
     return time.perf_counter() - t0, n_theta, len(terms), gates
 
 
@@ -173,8 +178,8 @@ def blas_threads():
     return os.cpu_count() or 1
 
 
-def cpu_baseline(wl):
-    dt, states, T, gates = oracle_sample(wl, 1)
+def cpu_baseline(wl, energies=None):
+    dt, states, T, gates = oracle_sample(wl, 1, energies=energies)
     out = {"value": states * T / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
            "gates_per_s": gates / dt,
            "sample": f"FP64 oracle (numpy/LAPACK) on 1 of the theta rows: full 390-gate "
@@ -278,6 +283,108 @@ def random_terms_pass(args, m, wl, energy, stream, ws, device):
     return out
 
 
+def measure_alu_peaks(device):
+    """FMA throughput of the CUDA cores in FP32 and FP64 (the ceilings of the
+    Jacobi SVD), from the library's peak kernel: full occupancy (8 CTAs of
+    256 threads per SM), best of 5 event-timed launches after 2 warm-ups."""
+    import torch
+    from paper_1807_07914_gb300 import tnmps
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = 8 * sms
+    out = {}
+    for bits, iters, dt in ((32, 40000, torch.float32), (64, 600, torch.float64)):
+        sink = torch.empty(blocks * 256, dtype=dt, device=device)
+        stream = torch.cuda.current_stream(device)
+        for _ in range(2):
+            flops = tnmps.alu_peak_dev(bits, blocks, iters, sink)
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tnmps.alu_peak_dev(bits, blocks, iters, sink)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[f"fp{bits}_tflops"] = flops / (best / 1000.0) / 1e12
+        out[f"fp{bits}_ms"] = best
+    out["how"] = (f"tnmps_alu_peak_dev: {blocks} CTAs x 256 threads, 8 independent FMA chains "
+                  "per thread, 2 flop per FMA, best of 5 event-timed launches")
+    return out
+
+
+def jacobi_roofline(st, prof_jac, steps, t_local, peak, peak_src):
+    """The Jacobi SVD's roofline object: algorithmic flops per launch (device
+    counters) over its average event-timed launch duration."""
+    jac_ms, jac_n = prof_jac
+    alg_flops = 8 * st["jacobi_pair_rows"] + 18 * st["jacobi_rot_rows"]
+    exe_flops = 16 * st["jacobi_pair_rows"] + 18 * st["jacobi_rot_rows"]
+    launches_per_step = jac_n / steps
+    avg_launch_s = jac_ms / 1000.0 / max(jac_n, 1)
+    per_launch_alg = alg_flops / max(launches_per_step, 1)
+    achieved = per_launch_alg / avg_launch_s / 1e12
+    return {"kernel": "k_jacobi (one-sided Jacobi SVD, K3)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": peak_src,
+            "executed_tflops": exe_flops / max(launches_per_step, 1) / avg_launch_s / 1e12,
+            "alg_flops_per_launch": per_launch_alg, "avg_launch_ms": 1000 * avg_launch_s,
+            "share_of_step": jac_ms / steps / (1000 * t_local / steps),
+            "sweeps_per_svd": st["jacobi_sweeps"] / max(st["svds"], 1)}
+
+
+def accuracy(e_gpu, e_oracle, terms):
+    if e_oracle is None:
+        return None
+    scale = sum(abs(t[0]) for t in terms)
+    d = abs(float(e_gpu) - float(e_oracle))
+    return {"theta_row": 0, "energy": float(e_gpu), "energy_oracle": float(e_oracle),
+            "abs_dE": d, "rel_to_sum_abs_c": d / scale, "target_rel": 1e-6,
+            "oracle": "FP64 oracle MPS (LAPACK SVD, rule R, per-term full sweeps) on the same row"}
+
+
+def fp64_form(args, wl, th_row0, e_oracle, alu, device):
+    """The plain FP64 form (complex128 state, FP64 Jacobi, sweeps and split)
+    on the same workload: one timed step of 152 states (one SVD per SM), the
+    kernels loaded first by a one-layer warm-up circuit."""
+    import torch
+    from paper_1807_07914_gb300 import tnmps
+    n, chi, P, T = wl["n"], wl["chi_max"], wl["n_params"], len(wl["terms"])
+    B = args.fp64_batch
+    th = inputs.thetas(B, P, inputs.rng_for(5, 200))
+    th[0] = th_row0
+    m = tnmps.MPSBatch(n, chi, B, dtype="c128", max_params=P, eps=wl["eps"], device=device)
+    ps = tnmps.PauliSum(n, wl["terms"])
+    th_dev = torch.tensor(th, dtype=torch.float64, device=device)
+    energy = torch.empty(B, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    warm, _ = inputs.hea_circuit(n, 1, ("RY", "RZ"))
+    m.apply_circuit_dev(tnmps.gate_array(warm), th_dev)
+    m.expect_dev(ps, energy)
+    torch.cuda.synchronize(device)
+    gates_c = tnmps.gate_array(wl["circuit"])
+    m.reset()
+    m.profile(("jacobi",))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.apply_circuit_dev(gates_c, th_dev)
+    m.expect_dev(ps, energy)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    prof = m.profile_read()
+    m.profile(None)
+    m.check()
+    st = m.stats()
+    t = e0.elapsed_time(e1) / 1000.0
+    roof = jacobi_roofline(st, prof["jacobi"], 1, t, alu["fp64_tflops"],
+                           "measured FP64 FMA rate (tnmps_alu_peak_dev, this run)")
+    return {"dtype": "c128", "batch": B, "steps": 1, "ms_per_step": 1000 * t,
+            "value": B * T / t, "unit": UNIT, "gates_per_s": B * 390 / t,
+            "gates_chi128_per_s": st["gates2q_full"] / t, "roofline": roof,
+            "accuracy": accuracy(energy[0].item(), e_oracle, wl["terms"])}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_setup()
@@ -296,9 +403,10 @@ def run_gpu(args):
     P = wl["n_params"]
     th = inputs.thetas(B, P, inputs.rng_for(5, 100 + rank))
     if rank == 0:
-        th[0] = wl["thetas"][0]        # the row the CPU baseline samples
+        th[0] = wl["thetas"][0]        # the row the CPU baseline and the accuracy check sample
     terms = wl["terms"]
     T = len(terms)
+    alu = measure_alu_peaks(device)
     m = tnmps.MPSBatch(n, chi, B, dtype=args.dtype, max_params=P, eps=eps, device=device)
     ps = tnmps.PauliSum(n, terms)
     gates_c = tnmps.gate_array(wl["circuit"])
@@ -349,6 +457,7 @@ def run_gpu(args):
         dist.barrier()
     st1 = m.stats()
     m.check()
+    e_row0 = energy[0].item()
     t_local = start.elapsed_time(end) / 1000.0
     circ_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     exp_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
@@ -359,29 +468,11 @@ def run_gpu(args):
     gates_per_s = total_states * 390 / t
     full_per_step = st1["gates2q_full"]
     # ---- dominant kernel: one-sided Jacobi (counters of the last step)
-    jac_ms, jac_n = prof["jacobi"]
-    alg_flops = 8 * st1["jacobi_pair_rows"] + 18 * st1["jacobi_rot_rows"]
-    exe_flops = 16 * st1["jacobi_pair_rows"] + 18 * st1["jacobi_rot_rows"]
-    launches_per_step_jac = jac_n / args.steps
-    avg_launch_s = jac_ms / 1000.0 / max(jac_n, 1)
-    per_launch_alg = alg_flops / max(launches_per_step_jac, 1)
-    achieved = per_launch_alg / avg_launch_s / 1e12
-    peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if args.dtype != "c128":
-        peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        peak_src = (f"derived: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
-                    f"{sm_max:.0f} MHz (max SM clock)")
+        peak, peak_src = alu["fp32_tflops"], "measured FP32 FMA rate (tnmps_alu_peak_dev, this run)"
     else:
-        peak = FP64_NOMINAL_TFLOPS
-        peak_src = "nominal GB300 dense FP64 (1.25 TFLOP/s)"
-    roof = {"kernel": "k_jacobi (one-sided Jacobi SVD, K3)", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": peak_src,
-            "executed_tflops": exe_flops / max(launches_per_step_jac, 1) / avg_launch_s / 1e12,
-            "alg_flops_per_launch": per_launch_alg, "avg_launch_ms": 1000 * avg_launch_s,
-            "share_of_step": jac_ms / args.steps / (1000 * t_local / args.steps),
-            "sweeps_per_svd": st1["jacobi_sweeps"] / max(st1["svds"], 1)}
+        peak, peak_src = alu["fp64_tflops"], "measured FP64 FMA rate (tnmps_alu_peak_dev, this run)"
+    roof = jacobi_roofline(st1, prof["jacobi"], args.steps, t_local, peak, peak_src)
     # ---- end to end through the public host API (pinned host buffers)
     th_pin = torch.tensor(th, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -413,14 +504,27 @@ def run_gpu(args):
             "phases_ms": {"circuit": circ_ms, "expect": exp_ms},
             "expectations_per_s_sweep_phase": B * T / (exp_ms / 1000.0),
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches_step * args.steps),
-            "clocks": clk,
+            "clocks": clk, "alu_peaks": alu,
         }
         if rand is not None:
             line["random_terms"] = rand
         if args.profile_all:
             line["class_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
+    del m
+    # ---- accuracy of this line against the FP64 oracle on theta row 0, the
+    # oracle timed on the host cores, and the plain FP64 form
+    e_oracle = None
+    if rank == 0:
+        energies = []
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl)
+            line["cpu_baseline"] = cpu_baseline(wl, energies)
+        elif not args.no_accuracy:
+            oracle_sample(wl, 1, energies=energies)
+        e_oracle = energies[0] if energies else None
+        line["accuracy"] = accuracy(e_row0, e_oracle, terms)
+    if not args.no_fp64_form and rank == 0:
+        line["fp64_form"] = fp64_form(args, wl, wl["thetas"][0], e_oracle, alu, device)
+    if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -445,6 +549,12 @@ def main():
     ap.add_argument("--batch", type=int, default=304,
                     help="theta rows per GPU (default 2 x 152 SMs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP64 oracle energy of theta row 0 (with --no-cpu-baseline)")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the one-step measurement of the plain FP64 (complex128) form")
+    ap.add_argument("--fp64-batch", type=int, default=152,
+                    help="states of the FP64-form step (default one per SM)")
     ap.add_argument("--profile-all", action="store_true",
                     help="time every kernel class with events (diagnostic; adds overhead)")
     args = ap.parse_args()

@@ -298,6 +298,20 @@ tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, vo
                                   int lda, double *sigma_dev, int32_t *sweeps_dev,
                                   int max_sweeps, void *stream);
 
+/* ---- ALU ceiling (measurement) ---------------------------------------------
+ * The paper has no counterpart: this measures the issue rate of fused
+ * multiply-adds on the CUDA cores, the ceiling of the ALU-bound Jacobi SVD,
+ * so that its roofline fraction is taken against a measured rate. One launch
+ * of `blocks` CTAs of 256 threads; every thread runs 8 independent FMA
+ * chains for 64 * iters FMAs, in FP32 (bits = 32) or FP64 (bits = 64).
+ *   sink_dev: device buffer of blocks * 256 elements of that type (written);
+ *   *flops (may be NULL): floating-point operations of the launch
+ *     (2 per FMA).
+ * The caller times the launch (CUDA events on `stream`); asynchronous.
+ * TNMPS_ERR_ARG on bits not 32/64, blocks or iters < 1, or a NULL sink. */
+tnmps_status tnmps_alu_peak_dev(int bits, int blocks, int iters, void *sink_dev, double *flops,
+                                void *stream);
+
 /* ---- many circuits in one persistent launch --------------------------------
  * Independent jobs with uneven register sizes, depths, bond caps and Pauli
  * sums (the VQE loop of Sec. V.B run for many programs at once), complex64

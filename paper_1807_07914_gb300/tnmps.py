@@ -122,6 +122,7 @@ def lib():
         "tnmps_batch_free": (None, [P]),
         "tnmps_profile": (I, [P, C.c_uint32]),
         "tnmps_profile_read": (I, [P, P, P]),
+        "tnmps_alu_peak_dev": (I, [I, I, I, P, C.POINTER(C.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -579,6 +580,21 @@ def gemm_bf16(a, b, out=None, stream=None):
     if st != 0:
         raise TnmpsError(st, "gemm_bf16 failed")
     return out
+
+
+def alu_peak_dev(bits, blocks, iters, sink, stream=None):
+    """Enqueue the FMA-throughput kernel (FP32 for bits = 32, FP64 for 64)
+    into ``sink`` (a float32 / float64 CUDA tensor of blocks * 256 values);
+    returns the launch's floating-point operation count."""
+    assert sink.is_cuda and sink.numel() >= blocks * 256
+    assert sink.dtype == {32: torch.float32, 64: torch.float64}[bits]
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(sink.device).cuda_stream
+    fl = C.c_double()
+    st = lib().tnmps_alu_peak_dev(int(bits), int(blocks), int(iters), _ptr(sink), C.byref(fl),
+                                  C.c_void_p(s))
+    if st != 0:
+        raise TnmpsError(st, "alu_peak_dev failed")
+    return fl.value
 
 
 def jacobi_svd_dev(a, m, n, sigma, sweeps, max_sweeps=0, stream=None):
