@@ -358,20 +358,28 @@ void tnmps_batch_free(tnmps_batch *batch);
  * memory budget a host framework has already reserved in full, or a loop
  * that must never enter the allocator. Same results and arguments as
  * tnmps_expect_pauli_sum_dev without the workspace: the library uses its own
- * scratch, a static device array of TNMPS_NOALLOC_SCRATCH_BYTES that every
- * GPU loading the library holds until the process exits. The paper has no
- * counterpart to this entry point.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture.
+ * scratch, a static device array of TNMPS_NOALLOC_SCRATCH_BYTES (160 MiB: one
+ * state of a 40-qubit, chi = 128 register with a 157-term Heisenberg chain
+ * needs about 100 MB in the BF16-split form and 127 MB in complex128) that
+ * every GPU loading the library holds until the process exits. The paper has
+ * no counterpart to this entry point.
+ *   - The first call on a device looks up the array's device address for the
+ *     current CUDA context (and again whenever the context changes, e.g.
+ *     after cudaDeviceReset); make that first call before any stream capture.
  *   - Term sets (with this context) needing more scratch than the array
  *     holds for a single state are rejected with TNMPS_ERR_NOMEM and a
- *     message giving both sizes. States are processed in chunks that fit.
- *   - All calls share the array and each overwrites it (the term plan is
- *     uploaded on every call); calls whose GPU work overlaps -- on other
- *     streams or from other contexts -- race on it.
+ *     message giving both sizes. States are processed in chunks that fit;
+ *     the per-term region is reserved only when per_term_dev is NULL.
+ *   - All calls share the array, which keeps the last call's contents. The
+ *     term plan is uploaded (from host memory; this synchronises the
+ *     context's stream) when the array last held another context's or
+ *     another term set's plan; a repeated call with the same context and
+ *     term set is asynchronous on the context's stream. Calls whose GPU
+ *     work overlaps -- other streams, other contexts, other host threads --
+ *     race on the array.
  *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
- *     call. Asynchronous on the context's stream. */
-#define TNMPS_NOALLOC_SCRATCH_BYTES (32u << 20)
+ *     call. */
+#define TNMPS_NOALLOC_SCRATCH_BYTES (160u << 20)
 tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *ctx, const tnmps_terms *terms,
                                             double *energy_dev, double *per_term_dev);
 

@@ -33,6 +33,7 @@ struct tnmps_supergate {
 namespace {
 
 std::atomic<uint64_t> g_plan_gen{1};
+std::atomic<uint64_t> g_ctx_uid{1};
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -617,6 +618,7 @@ tnmps_status tnmps_init(tnmps_ctx **out, int n, int chi, tnmps_dtype dtype, int 
   tnmps_ctx *c = new (std::nothrow) tnmps_ctx();
   if (!c) return TNMPS_ERR_NOMEM;
   Layout L = make_layout(n, chi, dtype, batch, max_params);
+  c->uid = g_ctx_uid++;
   c->n = n;
   c->chi = chi;
   c->batch = batch;

@@ -270,7 +270,13 @@ static std::vector<int64_t> tc_site_offsets(const tnmps_ctx *c, int64_t *stride)
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static WsLayout layout(const tnmps_ctx *c, const TermPlan &p, int bc) {
+// Workspace carving. The plan region (trie, terms, coefficients, right
+// environment offsets, tensor-core site geometry) comes first and depends only
+// on the context and the term set, so a cached upload stays valid for any
+// chunk size. The per-term and energy result regions are reserved only when
+// the caller supplies no device output for them (pt_region / e_region).
+static WsLayout layout(const tnmps_ctx *c, const TermPlan &p, int bc, bool pt_region = true,
+                       bool e_region = true) {
   WsLayout L{};
   const size_t esz = c->dtype == TNMPS_C128 ? 16 : 8;
   const size_t nn = p.node_site.size(), nt = p.tterm.size();
@@ -291,18 +297,17 @@ static WsLayout layout(const tnmps_ctx *c, const TermPlan &p, int bc) {
   o = al(o + 4 * p.identity_terms.size());
   L.o_coeffs = o;
   o = al(o + 8 * (size_t)p.n_terms);
-  L.plan_bytes = o;
-  L.per_term_off = o;
-  o = al(o + 8 * (size_t)c->batch * (size_t)p.n_terms);
-  L.energy_off = o;
-  o = al(o + 8 * (size_t)c->batch);
   L.roff_off = o;
   o = al(o + 8 * (size_t)c->n);
-  // (kept ahead of every chunk-dependent region: the plan upload is cached)
   L.o_tc_soff = o;
   o = al(o + 8 * (size_t)c->n);
   L.o_tc_geo = o;
   o = al(o + 8 * (size_t)c->n);
+  L.plan_bytes = o;
+  L.per_term_off = o;
+  if (pt_region) o = al(o + 8 * (size_t)c->batch * (size_t)p.n_terms);
+  L.energy_off = o;
+  if (e_region) o = al(o + 8 * (size_t)c->batch);
   int64_t re = 0;
   for (int i = 0; i < c->n; ++i) re += (int64_t)c->cap[i + 1] * c->cap[i + 1];
   L.renv_elems = re;
@@ -390,10 +395,11 @@ cudaError_t run_expect(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_byte
                        double **per_term_used) {
   const int B = c->batch;
   int bc = chunk > 0 ? (chunk < B ? chunk : B) : B;
-  WsLayout L = layout(c, p, bc);
+  const bool pt_region = per_term_dev == nullptr, e_region = energy_dev == nullptr;
+  WsLayout L = layout(c, p, bc, pt_region, e_region);
   while (L.total > ws_bytes && bc > 1) {
     bc = (bc + 1) / 2;
-    L = layout(c, p, bc);
+    L = layout(c, p, bc, pt_region, e_region);
   }
   if (L.total > ws_bytes) return cudaErrorMemoryAllocation;
   cudaStream_t st = c->stream;
@@ -551,9 +557,10 @@ cudaError_t run_expect(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_byte
 
 }  // namespace
 
-size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk) {
+size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk, bool pt_region,
+                       bool e_region) {
   const int bc = chunk > 0 ? (chunk < c->batch ? chunk : c->batch) : c->batch;
-  return layout(c, p, bc).total;
+  return layout(c, p, bc, pt_region, e_region).total;
 }
 
 cudaError_t expect_run(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_bytes, int chunk,

@@ -172,6 +172,8 @@ struct tnmps_ctx {
   tnmps_status inject_status = TNMPS_OK;
   int call_count = 0;
 
+  uint64_t uid = 0;               // unique per tnmps_init in this process (never reused)
+
   // last uploaded term plan (skip re-upload)
   const void *plan_terms = nullptr;
   void *plan_ws = nullptr;
@@ -287,6 +289,9 @@ struct TermPlan {
 cudaError_t expect_run(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_bytes, int chunk,
                        double *energy_dev, double *per_term_dev, double **energy_used,
                        double **per_term_used);
-size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk);
+// Workspace bytes of an expectation call; the per-term / energy result regions
+// are counted only when requested (the caller then supplies no device output).
+size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk, bool pt_region = true,
+                       bool e_region = true);
 tnmps_status expect_noalloc_impl(tnmps_ctx *c, const TermPlan &p, uint64_t gen,
                                  double *energy_dev, double *per_term_dev);

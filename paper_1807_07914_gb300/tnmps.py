@@ -343,7 +343,9 @@ class MPSBatch:
 
     def expect_noalloc(self, terms, energy, per_term=None):
         """Like expect_dev, for callers that cannot allocate device memory:
-        the library's own static scratch replaces the workspace (asynchronous)."""
+        the library's own static scratch replaces the workspace. Asynchronous
+        when the scratch already holds this context's plan for these terms;
+        otherwise the plan upload synchronises the stream first."""
         self._check(lib().tnmps_expect_pauli_sum_noalloc(self._h, terms._h, _ptr(energy),
                                                          _ptr(per_term)))
 

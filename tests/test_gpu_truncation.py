@@ -25,9 +25,13 @@ from paper_1807_07914_gb300 import tnmps  # noqa: E402
 
 DTYPES = ["c128", "c64", "c64_bf16split"]
 # per dtype: per-term, relative discarded weight, smallest decision margin the
-# arithmetic resolves (relative to sigma_0)
-BARS = {"c128": (1e-10, 1e-10, 1e-12), "c64": (1e-4, 1e-4, 1e-5),
-        "c64_bf16split": (1e-4, 1e-4, 1e-5)}
+# arithmetic resolves (relative to sigma_0), and an absolute floor on the
+# discarded weight per truncating step: a dropped value sigma carries an
+# absolute error d ~ sqrt(M) u sigma_0 from the FP32 Jacobi (u = 2^-24, M <= 16
+# rows here: d <= 2.4e-7), so sigma^2 is off by up to 2 sigma d + d^2 -- about
+# 1e-11 for the sigma ~ 3e-5 that eps = 1e-4 drops
+BARS = {"c128": (1e-10, 1e-10, 1e-12, 0.0), "c64": (1e-4, 1e-4, 1e-5, 1e-11),
+        "c64_bf16split": (1e-4, 1e-4, 1e-5, 1e-11)}
 
 
 def sum_abs(terms):
@@ -43,7 +47,7 @@ def gpu_run(n, chi, eps, circ, th, terms, dtype):
 
 
 def compare(n, chi, eps, circ, th, terms, dtype, expect_cut=True):
-    tol_p, tol_w, margin = BARS[dtype]
+    tol_p, tol_w, margin, w_floor = BARS[dtype]
     dims, w, e, pt = gpu_run(n, chi, eps, circ, th, terms, dtype)
     for b in range(th.shape[0]):
         vals, om = OE.term_values_mps(n, circ, th[b], terms, chi, eps)
@@ -54,7 +58,8 @@ def compare(n, chi, eps, circ, th, terms, dtype, expect_cut=True):
         msg = (f"{dtype} b={b} dims {list(dims[b])} vs {om.bond_dims()}, w {w[b]:.6e} vs "
                f"{om.discarded:.6e}, max|dP| {np.abs(pt[b] - vals).max():.2e}")
         assert list(dims[b]) == om.bond_dims(), msg
-        assert abs(w[b] - om.discarded) <= tol_w * om.discarded + 1e-30, msg
+        cuts = int(np.count_nonzero(np.array(om.step_weights) > 0))
+        assert abs(w[b] - om.discarded) <= tol_w * om.discarded + w_floor * cuts + 1e-30, msg
         assert np.abs(pt[b] - vals).max() <= tol_p, msg
         tol_e = 1e-10 if dtype == "c128" else 1e-6
         assert abs(e[b] - OE.energy_from_values(terms, vals)) <= tol_e * sum_abs(terms), msg
