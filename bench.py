@@ -239,7 +239,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def random_terms_pass(args, m, wl, energy, stream, ws, device):
+def random_terms_pass(args, m, wl, energy, stream, ws, device, chunk):
     """One timed expectation pass of the 2000 random strings over the batch's
     final states; the environment updates' algorithmic flops come from the
     library's counters and the sweep GEMMs are event-timed on its stream."""
@@ -247,14 +247,14 @@ def random_terms_pass(args, m, wl, energy, stream, ws, device):
     from paper_1807_07914_gb300 import tnmps
     ps = tnmps.PauliSum(wl["n"], wl["terms_random"])
     T = len(wl["terms_random"])
-    m.expect_dev(ps, energy, chunk=args.random_chunk)       # warm-up: workspace, plan upload
+    m.expect_dev(ps, energy, chunk=chunk)       # warm-up: workspace, plan upload
     torch.cuda.synchronize(device)
     s0 = m.stats()
     m.profile(("env", "env_tc"))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    m.expect_dev(ps, energy, chunk=args.random_chunk)
+    m.expect_dev(ps, energy, chunk=chunk)
     e1.record(stream)
     torch.cuda.synchronize(device)
     prof = m.profile_read()
@@ -263,7 +263,7 @@ def random_terms_pass(args, m, wl, energy, stream, ws, device):
     m.check()
     t = reduce_max(e0.elapsed_time(e1) / 1000.0, ws, device)
     flops = s1["env_flops"] - s0["env_flops"]
-    out = {"terms": T, "weight_max": 4, "chunk": args.random_chunk,
+    out = {"terms": T, "weight_max": 4, "chunk": chunk,
            "value": reduce_sum(m.batch, ws, device) * T / t, "unit": UNIT, "ms_per_pass": 1000 * t,
            "env_updates": s1["env_updates"] - s0["env_updates"],
            "env_alg_tflops": flops / t / 1e12}
@@ -413,6 +413,31 @@ def run_gpu(args):
     th_dev = torch.tensor(th, dtype=torch.float64, device=device)
     energy = torch.empty(B, dtype=torch.float64, device=device)
     stream = torch.cuda.current_stream(device)
+    # ---- launch shapes picked by the autotuner on this workload (untimed)
+    heis_chunk, rand_chunk, tune = 0, args.random_chunk, None
+    if not args.no_tune:
+        from paper_1807_07914_gb300 import autotune
+        sets = {"heisenberg": ps}
+        if not args.no_random_terms:
+            sets["random"] = tnmps.PauliSum(n, wl["terms_random"])
+        rep = autotune.tune_context(m, gates_c, th_dev, sets)
+        heis_chunk = rep["chunk"]["heisenberg"]
+        rand_chunk = rep["chunk"].get("random", args.random_chunk)
+        ex = rep["expect_s"]["heisenberg"]["candidates_s"]
+        d_key = "0" if "0" in ex else max(ex, key=int)   # the whole batch when it fits
+        default_s = rep["circuit_s"]["default"] + ex[d_key]
+        tuned_s = rep["circuit_s"]["tuned"] + ex[str(heis_chunk)]
+        tune = {"tuning": rep["tuning"], "chunk": rep["chunk"], "cached": rep["cached"],
+                "default_step_s": default_s, "tuned_step_s": tuned_s,
+                "gain": default_s / tuned_s, "trials": rep["trials"],
+                "expect_candidates_s": {k: v["candidates_s"] for k, v in rep["expect_s"].items()},
+                "how": rep["how"] + "; default = all shapes 0, Heisenberg chunk = whole batch, "
+                                    f"random-string chunk = {args.random_chunk}"}
+        if "random" in rep["expect_s"]:
+            rc = rep["expect_s"]["random"]["candidates_s"]
+            if str(args.random_chunk) in rc:
+                tune["random_pass_gain"] = rc[str(args.random_chunk)] / rc[str(rand_chunk)]
+        del sets
 
     def step(ev=None):
         if ev is not None:  # timed steps sit in an NVTX range (launch lists filter on it)
@@ -423,7 +448,7 @@ def run_gpu(args):
         m.apply_circuit_dev(gates_c, th_dev)
         if ev is not None:
             ev[1].record(stream)
-        m.expect_dev(ps, energy)
+        m.expect_dev(ps, energy, chunk=heis_chunk)
         if ev is not None:
             ev[2].record(stream)
             torch.cuda.nvtx.range_pop()
@@ -481,7 +506,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         m.reset()
         m.apply_circuit(wl["circuit"], th_pin.numpy())
-        e_host = m.expect(ps)
+        e_host = m.expect(ps, chunk=heis_chunk)
     t_e2e = reduce_max(time.perf_counter() - t0, ws, device)
     e2e = {"value": reduce_sum(B, ws, device) * e2e_steps * T / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(B * P * 8), "d2h_bytes_per_step": int(B * 8),
@@ -490,7 +515,7 @@ def run_gpu(args):
     # ---- the second term set of the metric: 2000 random strings of weight <= 4
     # on the final states (expectation phase alone, states resident)
     rand = None if args.no_random_terms else random_terms_pass(args, m, wl, energy, stream, ws,
-                                                                device)
+                                                                device, rand_chunk)
     line = None
     if rank == 0:
         line = {
@@ -506,6 +531,8 @@ def run_gpu(args):
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches_step * args.steps),
             "clocks": clk, "alu_peaks": alu,
         }
+        if tune is not None:
+            line["autotune"] = tune
         if rand is not None:
             line["random_terms"] = rand
         if args.profile_all:
@@ -545,7 +572,9 @@ def main():
     ap.add_argument("--no-random-terms", action="store_true",
                     help="skip the pass over the 2000 random strings")
     ap.add_argument("--random-chunk", type=int, default=32,
-                    help="states per expectation chunk of the random-string pass")
+                    help="states per expectation chunk of the random-string pass (untuned default)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shapes (skip the autotuner)")
     ap.add_argument("--batch", type=int, default=304,
                     help="theta rows per GPU (default 2 x 152 SMs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

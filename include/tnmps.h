@@ -278,6 +278,29 @@ tnmps_status tnmps_get_site(tnmps_ctx *ctx, int b, int site, double *out, size_t
 /* Orthogonality centre (site index) after the work enqueued so far. */
 int tnmps_get_centre(const tnmps_ctx *ctx);
 tnmps_status tnmps_get_stats(tnmps_ctx *ctx, tnmps_stats *out);
+/* ---- launch shapes (autotuning) ---------------------------------------------
+ * Runtime choices of launch shape for the hot kernels of a context; every
+ * choice computes the same results (up to FP32 summation order), only the
+ * speed differs. An autotuner times the choices on the caller's workload and
+ * sets the fastest. The paper has no counterpart (its simulator was serial).
+ *   jacobi_shape[c]: the complex64 Jacobi SVD for blocks of up to 64, 128,
+ *     256 rows (c = 0, 1, 2):
+ *       0 (default) c = 0, 1: one CTA of 512 threads per SM, 32-column blocks;
+ *                   c = 2: two CTAs of 256 threads per SM, 16-column blocks;
+ *       1           c = 0, 1: two CTAs of 256 threads per SM, 16-column blocks;
+ *                   c = 2: one CTA of 512 threads per SM, 32-column blocks.
+ *     (complex128 and blocks above 256 rows have a single shape.)
+ *   gemm_stages: shared-memory ring depth of the tensor-core GEMMs of the
+ *     BF16-split form (two-site block, split, sweeps): 0 (default) = as many
+ *     as fit, at most 3; or 2 or 3 (capped at what fits).
+ * TNMPS_ERR_ARG on any other value. */
+typedef struct {
+  int32_t jacobi_shape[3];
+  int32_t gemm_stages;
+} tnmps_tuning;
+tnmps_status tnmps_set_tuning(tnmps_ctx *ctx, const tnmps_tuning *tuning);
+tnmps_status tnmps_get_tuning(const tnmps_ctx *ctx, tnmps_tuning *tuning);
+
 /* Time the kernel classes in class_mask (bit i = tnmps_prof_class i) with
  * CUDA events recorded on the context's stream around each launch group;
  * totals are cleared. class_mask = 0 stops timing. */

@@ -1319,6 +1319,23 @@ tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, vo
   return e == cudaSuccess ? TNMPS_OK : TNMPS_ERR_CUDA;
 }
 
+tnmps_status tnmps_set_tuning(tnmps_ctx *c, const tnmps_tuning *t) {
+  if (!c || !t) return TNMPS_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (t->jacobi_shape[k] != 0 && t->jacobi_shape[k] != 1)
+      return fail(c, TNMPS_ERR_ARG, "jacobi_shape must be 0 or 1");
+  if (t->gemm_stages != 0 && t->gemm_stages != 2 && t->gemm_stages != 3)
+    return fail(c, TNMPS_ERR_ARG, "gemm_stages must be 0, 2 or 3");
+  c->tuning = *t;
+  return TNMPS_OK;
+}
+
+tnmps_status tnmps_get_tuning(const tnmps_ctx *c, tnmps_tuning *t) {
+  if (!c || !t) return TNMPS_ERR_ARG;
+  *t = c->tuning;
+  return TNMPS_OK;
+}
+
 tnmps_status tnmps_debug_inject(tnmps_ctx *c, int nth, tnmps_status status) {
   if (!c || nth < 0) return TNMPS_ERR_ARG;
   c->inject_nth = nth > 0 ? c->call_count + nth : 0;

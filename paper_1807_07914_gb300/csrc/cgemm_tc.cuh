@@ -111,14 +111,14 @@ struct Unit {
   unsigned long long flops;  // algorithmic flops counted for this item (0: none)
 };
 
-template <int NMAX, int EPI_SMEM, int P>
+template <int NMAX, int EPI_SMEM, int P, int SREQ = 3>
 struct Ring {
   static constexpr uint32_t A_PIECE = TILE;
   static constexpr uint32_t B_PIECE = NMAX * 128;
   static constexpr uint32_t STAGE = P * (A_PIECE + B_PIECE);
-  // as many stages as fit next to the epilogue staging (at most 3)
+  // SREQ stages, capped at what fits next to the epilogue staging
   static constexpr int S_FIT = (int)((227 * 1024 - 1024 - EPI_SMEM) / STAGE);
-  static constexpr int S = S_FIT > 3 ? 3 : S_FIT;
+  static constexpr int S = S_FIT > SREQ ? SREQ : S_FIT;
   static_assert(S >= 2, "stage ring needs two stages");
   static constexpr int SMEM = 1024 + S * STAGE + EPI_SMEM;
 };
@@ -145,10 +145,10 @@ __device__ __forceinline__ bool wait_or_fail(uint64_t *bar, uint32_t parity,
 //     epilogue has drained that accumulator (item i - 2);
 //   warps 0-3: the epilogue of item i (warp w reads TMEM lanes 32w..32w+31),
 //     overlapping the MMAs of item i + 1.
-template <class Prob, int NMAX>
+template <class Prob, int NMAX, int SREQ>
 __global__ void __launch_bounds__(192, 1) k_cgemm(Prob p, int items, uint32_t *err) {
   constexpr int P = Prob::PIECES;
-  using RG = Ring<NMAX, Prob::EPI_SMEM, P>;
+  using RG = Ring<NMAX, Prob::EPI_SMEM, P, SREQ>;
   constexpr int S = RG::S;
   extern __shared__ uint8_t smraw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
@@ -284,11 +284,9 @@ __global__ void __launch_bounds__(192, 1) k_cgemm(Prob p, int items, uint32_t *e
   if (warp == 0) tc::tmem_dealloc(tmem, NTM);
 }
 
-template <class Prob, int NMAX>
-cudaError_t launch_cgemm(const Prob &p, int64_t items, uint32_t *err, cudaStream_t s,
-                         uint64_t *launches) {
-  if (items <= 0) return cudaSuccess;
-  if (items > 0x7fffffff) return cudaErrorInvalidValue;
+template <class Prob, int NMAX, int SREQ>
+cudaError_t launch_cgemm_s(const Prob &p, int64_t items, uint32_t *err, cudaStream_t s,
+                           uint64_t *launches) {
   static int n_sm = 0;
   if (n_sm == 0) {
     int dev = 0;
@@ -297,14 +295,24 @@ cudaError_t launch_cgemm(const Prob &p, int64_t items, uint32_t *err, cudaStream
         n_sm <= 0)
       n_sm = 1;
   }
-  constexpr int SMEM = Ring<NMAX, Prob::EPI_SMEM, Prob::PIECES>::SMEM;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_cgemm<Prob, NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  constexpr int SMEM = Ring<NMAX, Prob::EPI_SMEM, Prob::PIECES, SREQ>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_cgemm<Prob, NMAX, SREQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   if (e != cudaSuccess) return e;
   const int grid = (int)(items < n_sm ? items : n_sm);
-  k_cgemm<Prob, NMAX><<<grid, 192, SMEM, s>>>(p, (int)items, err);
+  k_cgemm<Prob, NMAX, SREQ><<<grid, 192, SMEM, s>>>(p, (int)items, err);
   if (launches) ++*launches;
   return cudaGetLastError();
+}
+
+// stages: requested ring depth (0: as many as fit, at most 3; 2 or 3)
+template <class Prob, int NMAX>
+cudaError_t launch_cgemm(const Prob &p, int64_t items, uint32_t *err, cudaStream_t s,
+                         uint64_t *launches, int stages = 0) {
+  if (items <= 0) return cudaSuccess;
+  if (items > 0x7fffffff) return cudaErrorInvalidValue;
+  if (stages == 2) return launch_cgemm_s<Prob, NMAX, 2>(p, items, err, s, launches);
+  return launch_cgemm_s<Prob, NMAX, 3>(p, items, err, s, launches);
 }
 
 }  // namespace ctc

@@ -349,6 +349,7 @@ static cudaError_t run_levels_tc(tnmps_ctx *c, const TermPlan &p, const WsLayout
                                  const int32_t *d_tnode, const int32_t *d_tsite, double *per_term) {
   cudaStream_t st = c->stream;
   TcSweep t{};
+  t.stages = c->tuning.gemm_stages;
   t.dims = c->dims;
   t.n = c->n;
   t.b0 = e.b0;

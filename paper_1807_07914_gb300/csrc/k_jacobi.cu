@@ -103,12 +103,25 @@ cudaError_t run(const JacobiArgs &a, int batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// shape[c] (complex64, blocks of up to 64 / 128 / 256 rows): the launch shape
+// chosen by tnmps_set_tuning (0: default, 1: alternative; see tnmps.h)
 template <typename R>
-cudaError_t dispatch(const JacobiArgs &a, int Mcap, int batch, cudaStream_t s) {
+cudaError_t dispatch(const JacobiArgs &a, int Mcap, int batch, cudaStream_t s,
+                     const int32_t *shape = nullptr) {
+  const bool alt0 = sizeof(R) == 4 && shape && shape[0] == 1;
+  const bool alt1 = sizeof(R) == 4 && shape && shape[1] == 1;
+  const bool alt2 = sizeof(R) == 4 && shape && shape[2] == 1;
+  if constexpr (sizeof(R) == 4) {
+    if (Mcap <= 64 && alt0) return run<R, 16, 2, 256, 2, true>(a, batch, s);
+    if (Mcap > 64 && Mcap <= 128 && alt1) return run<R, 16, 4, 256, 2, true>(a, batch, s);
+  }
   if (Mcap <= 64) return run<R, 32, 2, 512, 1, true>(a, batch, s);
   if (Mcap <= 128) return run<R, 32, 4, 512, 1, true>(a, batch, s);
-  if constexpr (sizeof(R) == 4)  // 16-column blocks, 8 warps, two CTAs per SM
-    if (Mcap <= 256) return run<R, 16, 8, 256, 2, true>(a, batch, s);
+  if constexpr (sizeof(R) == 4) {  // default: 16-column blocks, 8 warps, two CTAs per SM
+    if (Mcap <= 256)
+      return alt2 ? run<R, 32, 8, 512, 1, true>(a, batch, s)
+                  : run<R, 16, 8, 256, 2, true>(a, batch, s);
+  }
   if (Mcap <= 256) return run<R, sizeof(R) == 8 ? 16 : 32, 8, 512, 1, true>(a, batch, s);
   return run<R, sizeof(R) == 8 ? 8 : 16, 16, sizeof(R) == 8 ? 256 : 512, 1, true>(a, batch, s);
 }
@@ -128,7 +141,7 @@ cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap) {
   a.err = c->err;
   a.counters = c->counters;
   if (c->dtype == TNMPS_C128) return dispatch<double>(a, Mcap, c->batch, c->stream);
-  return dispatch<float>(a, Mcap, c->batch, c->stream);
+  return dispatch<float>(a, Mcap, c->batch, c->stream, c->tuning.jacobi_shape);
 }
 
 cudaError_t launch_jacobi_standalone(tnmps_dtype dt, int batch, int m, int n, void *A, int lda,

@@ -299,14 +299,19 @@ cudaError_t tc_level(const TcSweep &t, const int32_t *node_site, const int32_t *
   const int units = nodes * t.nb;
   cudaError_t e;
   Step1 p1{t, lv};
-  e = t.nmax <= 128 ? ctc::launch_cgemm<Step1, 128>(p1, (int64_t)units * lv.grid_m, t.err, s, launches)
-                    : ctc::launch_cgemm<Step1, 256>(p1, (int64_t)units * lv.grid_m, t.err, s, launches);
+  e = t.nmax <= 128
+          ? ctc::launch_cgemm<Step1, 128>(p1, (int64_t)units * lv.grid_m, t.err, s, launches,
+                                          t.stages)
+          : ctc::launch_cgemm<Step1, 256>(p1, (int64_t)units * lv.grid_m, t.err, s, launches,
+                                          t.stages);
   if (e != cudaSuccess) return e;
   lv.grid_m = mt;
   Step2 p2{t, lv};
   return t.nmax <= 128
-             ? ctc::launch_cgemm<Step2, 128>(p2, (int64_t)units * lv.grid_m, t.err, s, launches)
-             : ctc::launch_cgemm<Step2, 256>(p2, (int64_t)units * lv.grid_m, t.err, s, launches);
+             ? ctc::launch_cgemm<Step2, 128>(p2, (int64_t)units * lv.grid_m, t.err, s, launches,
+                                             t.stages)
+             : ctc::launch_cgemm<Step2, 256>(p2, (int64_t)units * lv.grid_m, t.err, s, launches,
+                                             t.stages);
 }
 
 cudaError_t tc_term_dot(const TcSweep &t, const void *renv, const int64_t *roff,

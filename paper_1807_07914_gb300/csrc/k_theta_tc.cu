@@ -289,7 +289,7 @@ cudaError_t launch_split_tc(tnmps_ctx *c, int l, int kub) {
   p.grid_m = gm;
   p.grid_n = gn;
   return ctc::launch_cgemm<SplitProb<128>, 128>(p, (int64_t)c->batch * gm * gn, c->err, c->stream,
-                                                &c->launches);
+                                                &c->launches, c->tuning.gemm_stages);
 }
 
 cudaError_t launch_theta_tc(tnmps_ctx *c, int l) {
@@ -316,5 +316,5 @@ cudaError_t launch_theta_tc(tnmps_ctx *c, int l) {
   const int gn = (npad + 127) / 128;  // 128-wide N tiles: three pieces fill the stages
   ThetaProb<128> p{t, gm, gn};
   return ctc::launch_cgemm<ThetaProb<128>, 128>(p, (int64_t)c->batch * gm * gn, c->err, c->stream,
-                                                &c->launches);
+                                                &c->launches, c->tuning.gemm_stages);
 }

@@ -42,6 +42,7 @@ struct TcSweep {
   int64_t env_bytes;
   int rt;                   // row tiles of an environment (ceil(chi/128))
   int nmax;                 // 128 or 256: widest MMA N (>= every bond dimension)
+  int stages;               // GEMM ring depth request (0: as many as fit)
   uint32_t *err;
 };
 

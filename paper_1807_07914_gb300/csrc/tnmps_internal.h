@@ -173,6 +173,7 @@ struct tnmps_ctx {
   int call_count = 0;
 
   uint64_t uid = 0;               // unique per tnmps_init in this process (never reused)
+  tnmps_tuning tuning{};          // launch shapes (all zero: defaults)
 
   // last uploaded term plan (skip re-upload)
   const void *plan_terms = nullptr;

@@ -39,6 +39,10 @@ class Job(C.Structure):
                 ("coeffs", C.c_void_p), ("n_terms", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("jacobi_shape", C.c_int32 * 3), ("gemm_stages", C.c_int32)]
+
+
 class Stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("gates2q", "gates2q_full", "jacobi_pair_rows",
                                           "jacobi_rotations", "jacobi_sweeps", "svds",
@@ -123,6 +127,8 @@ def lib():
         "tnmps_profile": (I, [P, C.c_uint32]),
         "tnmps_profile_read": (I, [P, P, P]),
         "tnmps_alu_peak_dev": (I, [I, I, I, P, C.POINTER(C.c_double), P]),
+        "tnmps_set_tuning": (I, [P, C.POINTER(Tuning)]),
+        "tnmps_get_tuning": (I, [P, C.POINTER(Tuning)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -431,6 +437,20 @@ class MPSBatch:
         cnt = np.zeros(len(PROF_CLASSES), np.uint64)
         self._check(lib().tnmps_profile_read(self._h, _ptr(ms), _ptr(cnt)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def set_tuning(self, jacobi_shape=(0, 0, 0), gemm_stages=0):
+        """Launch shapes of the context's kernels (see tnmps_tuning in
+        include/tnmps.h); the results do not depend on them."""
+        t = Tuning()
+        for i, v in enumerate(jacobi_shape):
+            t.jacobi_shape[i] = int(v)
+        t.gemm_stages = int(gemm_stages)
+        self._check(lib().tnmps_set_tuning(self._h, C.byref(t)))
+
+    def get_tuning(self):
+        t = Tuning()
+        self._check(lib().tnmps_get_tuning(self._h, C.byref(t)))
+        return {"jacobi_shape": [int(v) for v in t.jacobi_shape], "gemm_stages": int(t.gemm_stages)}
 
     def inject(self, nth, status):
         self._check(lib().tnmps_debug_inject(self._h, int(nth), int(status)))
