@@ -51,6 +51,37 @@ def load_peaks():
         return {}
 
 
+def profiled_traffic(name):
+    """DRAM bytes (read + write) of a kernel from its committed ncu summary in
+    profiles/: the figures of its machine-readable lines, kept only while the
+    sha256 of the kernel's sources equals the one recorded with the capture
+    (a changed kernel has no traffic figure until it is captured again)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ":" in ln and ln.split(":", 1)[0].strip() in (
+                "traffic_bytes", "traffic_unit", "sources", "sources_sha256"):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if not {"traffic_bytes", "sources", "sources_sha256"} <= kv.keys():
+        return None
+    h = hashlib.sha256()
+    for src in kv["sources"].split():
+        try:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        except OSError:
+            return None
+    if h.hexdigest() != kv["sources_sha256"]:
+        return None
+    return {"bytes": float(kv["traffic_bytes"]), "unit": kv.get("traffic_unit", "per launch"),
+            "source": "profiles/" + name}
+
+
 def workload_cfg(args):
     wl = inputs.workload("chi128", rep=args.rank_seed)
     n, chi, eps = wl["n"], wl["chi_max"], wl["eps"]
@@ -280,6 +311,17 @@ def random_terms_pass(args, m, wl, energy, stream, ws, device, chunk):
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
             "note": "achieved = algorithmic complex-GEMM flops (4 real MACs per complex MAC); "
                     "executed = 3 x (hi*hi + hi*lo + lo*hi), padding to 32-wide tiles not counted"}
+        tr = profiled_traffic("k_swtc_bf16split_chi128_8states.md")
+        if tr is not None:
+            upd = out["env_updates"]
+            out["roofline"]["traffic"] = tr["bytes"] * upd
+            out["roofline"]["traffic_source"] = (
+                tr["source"] + f": {tr['bytes'] / 1e3:.0f} KB of DRAM {tr['unit']} (ncu, one "
+                "trie level of 8 states) x the node-state updates of this pass")
+            # algorithmic: the parent environment read and the new one written (BF16 hi/lo
+            # row-K form, 128 KB each at chi = 128) per update
+            out["roofline"]["alg_bytes"] = 2 * 131072 * upd
+            out["roofline"]["traffic_over_alg_bytes"] = tr["bytes"] / (2 * 131072)
     return out
 
 
@@ -324,9 +366,10 @@ def jacobi_roofline(st, prof_jac, steps, t_local, peak, peak_src):
     avg_launch_s = jac_ms / 1000.0 / max(jac_n, 1)
     per_launch_alg = alg_flops / max(launches_per_step, 1)
     achieved = per_launch_alg / avg_launch_s / 1e12
+    alg_bytes = st["jacobi_alg_bytes"] / max(launches_per_step, 1)
     return {"kernel": "k_jacobi (one-sided Jacobi SVD, K3)", "bound": "alu",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": peak_src,
+            "traffic": None, "alg_bytes_per_launch": alg_bytes, "peak_source": peak_src,
             "executed_tflops": exe_flops / max(launches_per_step, 1) / avg_launch_s / 1e12,
             "alg_flops_per_launch": per_launch_alg, "avg_launch_ms": 1000 * avg_launch_s,
             "share_of_step": jac_ms / steps / (1000 * t_local / steps),
@@ -498,6 +541,13 @@ def run_gpu(args):
     else:
         peak, peak_src = alu["fp64_tflops"], "measured FP64 FMA rate (tnmps_alu_peak_dev, this run)"
     roof = jacobi_roofline(st1, prof["jacobi"], args.steps, t_local, peak, peak_src)
+    tr = profiled_traffic("k_jacobi_bench_step_304states_dram.md")
+    if tr is not None and args.dtype == "c64_bf16split" and B == 304:
+        roof["traffic"] = tr["bytes"]
+        roof["traffic_over_alg_bytes"] = tr["bytes"] / roof["alg_bytes_per_launch"]
+        roof["traffic_source"] = (tr["source"] + ": ncu dram__bytes_read.sum + "
+                                  "dram__bytes_write.sum, every Jacobi launch of one timed step, "
+                                  "averaged per launch")
     # ---- end to end through the public host API (pinned host buffers)
     th_pin = torch.tensor(th, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))

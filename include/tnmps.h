@@ -110,6 +110,8 @@ typedef struct {
   uint64_t env_flops;        /* algorithmic real flops of those updates        */
   uint64_t jacobi_rot_rows;  /* sum over rotated pairs of the column length     */
   uint64_t launches;         /* kernel launches issued by this context (host count) */
+  uint64_t jacobi_alg_bytes; /* algorithmic bytes of the SVDs: each block read and
+                                written once                                   */
 } tnmps_stats;
 
 /* Kernel classes for event timing. */

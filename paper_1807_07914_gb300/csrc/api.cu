@@ -1264,6 +1264,7 @@ tnmps_status tnmps_get_stats(tnmps_ctx *c, tnmps_stats *out) {
   out->env_flops = h[CNT_ENV_FLOPS];
   out->jacobi_rot_rows = h[CNT_ROT_ROWS];
   out->launches = c->launches;
+  out->jacobi_alg_bytes = h[CNT_JAC_BYTES];
   return TNMPS_OK;
 }
 

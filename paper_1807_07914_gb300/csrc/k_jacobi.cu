@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(NT, MINB) k_jacobi(JacobiArgs p) {
       atomicAdd(&p.counters[CNT_ROT_ROWS], (unsigned long long)total_rot * M);
       atomicAdd(&p.counters[CNT_SWEEPS], (unsigned long long)sweep);
       atomicAdd(&p.counters[CNT_SVDS], 1ull);
+      // algorithmic bytes: the matrix read once and written once
+      atomicAdd(&p.counters[CNT_JAC_BYTES], 2ull * M * N * sizeof(cx<R>));
     }
   }
 }

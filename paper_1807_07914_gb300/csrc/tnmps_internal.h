@@ -64,6 +64,7 @@ enum {
   CNT_ENV_UPDATES,
   CNT_ENV_FLOPS,
   CNT_ROT_ROWS,
+  CNT_JAC_BYTES,
   CNT_NUM
 };
 

@@ -47,7 +47,7 @@ class Stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("gates2q", "gates2q_full", "jacobi_pair_rows",
                                           "jacobi_rotations", "jacobi_sweeps", "svds",
                                           "env_updates", "env_flops", "jacobi_rot_rows",
-                                          "launches")]
+                                          "launches", "jacobi_alg_bytes")]
 
 
 PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term", "env_tc", "fit")

@@ -27,19 +27,25 @@ from . import inputs, tnmps
 
 
 class MPSEnergy:
-    """E(theta) for rows of theta on the GPU MPS; counts evaluations."""
+    """E(theta) for rows of theta on the GPU MPS; counts evaluations. Calls
+    with fewer rows than ``small`` run on a second context of ``small``
+    states, so a single proposal does not pay for a full parameter-shift
+    batch."""
 
     def __init__(self, n, chi, eps, circuit, n_params, terms, dtype="c128", batch=640,
-                 device="cuda:0"):
+                 device="cuda:0", small=0):
         self.P = int(n_params)
-        self.batch = int(batch)
         self.device = torch.device(device)
-        self.m = tnmps.MPSBatch(n, chi, self.batch, dtype=dtype, max_params=self.P, eps=eps,
-                                device=self.device)
         self.ps = tnmps.PauliSum(n, terms)
         self.gates = tnmps.gate_array(circuit)
-        self.th = torch.zeros((self.batch, self.P), dtype=torch.float64, device=self.device)
-        self.e = torch.empty(self.batch, dtype=torch.float64, device=self.device)
+        self.ctx = []
+        for b in sorted({int(batch), int(small)} - {0}):
+            m = tnmps.MPSBatch(n, chi, b, dtype=dtype, max_params=self.P, eps=eps,
+                               device=self.device)
+            th = torch.zeros((b, self.P), dtype=torch.float64, device=self.device)
+            e = torch.empty(b, dtype=torch.float64, device=self.device)
+            self.ctx.append((b, m, th, e))
+        self.batch = int(batch)
         self.evals = 0
 
     def __call__(self, thetas):
@@ -48,15 +54,17 @@ class MPSEnergy:
         for s in range(0, thetas.shape[0], self.batch):
             chunk = thetas[s:s + self.batch]
             k = chunk.shape[0]
-            buf = np.empty((self.batch, self.P))
+            B, m, th, e = next(c for c in self.ctx if c[0] >= k)
+            buf = np.empty((B, self.P))
             buf[:k] = chunk
             buf[k:] = chunk[-1]
-            self.th.copy_(torch.from_numpy(buf))
-            self.m.reset()
-            self.m.apply_circuit_dev(self.gates, self.th)
-            self.m.expect_dev(self.ps, self.e)
-            out[s:s + k] = self.e[:k].cpu().numpy()
-        self.m.check()
+            th.copy_(torch.from_numpy(buf))
+            m.reset()
+            m.apply_circuit_dev(self.gates, th)
+            m.expect_dev(self.ps, e)
+            out[s:s + k] = e[:k].cpu().numpy()
+        for c in self.ctx:
+            c[1].check()
         self.evals += thetas.shape[0]
         return out
 
@@ -178,21 +186,26 @@ def surrogate_adam(energy, sur, theta0, lr, max_evals, target=None, sur_steps=8,
     theta = np.array(theta0, dtype=np.float64)
     opt = Adam(theta.size, lr)
     hist = []
-    best = np.inf
+    best, best_th = np.inf, theta.copy()
     stats = {"iterations": 0, "proposals": 0, "accepted": 0}
+
+    def seen(e, th):
+        nonlocal best, best_th
+        if e < best:
+            best, best_th = e, th.copy()
+        hist.append((energy.evals, best))
+
     while energy.evals < max_evals:
         e0, g, rows, es = param_shift(energy, theta)
         sur.add(rows, es)
-        best = min(best, e0)
-        hist.append((energy.evals, best))
+        seen(e0, theta)
         if target is not None and best <= target:
             break
         theta, st = opt.propose(theta, g)
         opt.commit(st)
         e = float(energy(theta[None])[0])
         sur.add(theta[None], np.array([e]))
-        best = min(best, e)
-        hist.append((energy.evals, best))
+        seen(e, theta)
         for _ in range(sur_steps):
             cand, _ = opt.propose(theta, sur.grad(theta))
             ec = float(energy(cand[None])[0])
@@ -202,11 +215,10 @@ def surrogate_adam(energy, sur, theta0, lr, max_evals, target=None, sur_steps=8,
                 break
             theta, e = cand, ec
             stats["accepted"] += 1
-            best = min(best, e)
-            hist.append((energy.evals, best))
+            seen(e, theta)
         stats["iterations"] += 1
         sur.fit(finetune_epochs, finetune_lr, recent=recent, rng=rng)
-    return hist, (best, theta), stats
+    return hist, (best, best_th), stats
 
 
 def evals_to(hist, target):
@@ -216,45 +228,96 @@ def evals_to(hist, target):
     return None
 
 
-def main():
-    import argparse
-    ap = argparse.ArgumentParser(description="surrogate-assisted vs plain VQE on the MPS")
-    ap.add_argument("--n-data", type=int, default=100000)
-    ap.add_argument("--budget", type=int, default=200000)
-    ap.add_argument("--lr", type=float, default=0.02)
-    ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--seed", type=int, default=0)
-    a = ap.parse_args()
-    wl = inputs.workload("heis40")
+def compare(wl, starts=3, budget=200000, lr=0.02, ref_lrs=(0.01, 0.03, 0.05, 0.08),
+            ref_budget=300000, n_data=100000, epochs=20, seed=0, dtype="c64", log=None):
+    """Surrogate-assisted against plain Adam from several random starts.
+
+    The target of each start is fixed before, and independently of, the two
+    compared runs: E* = the lowest energy of long plain-Adam runs from the
+    same start at other learning rates (``ref_lrs``, ``ref_budget``
+    evaluations each). The compared runs (plain Adam at ``lr``; the surrogate
+    method at ``lr`` from the same pretrained surrogate) get the same budget.
+    The optimisers evaluate on the ``dtype`` MPS (complex64: its energies are
+    within 1e-6 sum|c_k| of the FP64 oracle, far inside the 1e-4 criterion);
+    E* and every run's best point are re-evaluated on the complex128 MPS.
+    Reported per start: the evaluations each method needs to come within 1e-4
+    of E* in the optimisers' form (None: not within the budget) and its best
+    energy."""
     P = wl["n_params"]
+    args = (wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"])
     t0 = time.time()
-    gen = MPSEnergy(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"], "c64", 2048)
-    rng = np.random.default_rng(4000 + a.seed)
-    X = rng.uniform(-np.pi, np.pi, (a.n_data, P))
+    rng = np.random.default_rng(4000 + seed)
+    gen = MPSEnergy(*args, dtype, 2048)
+    X = rng.uniform(-np.pi, np.pi, (n_data, P))
     Y = gen(X)
     t_data = time.time() - t0
     sur = Surrogate(P)
     sur.add(X, Y)
     t1 = time.time()
-    train_mse = sur.fit(a.epochs, 1e-3, restandardise=True)
+    train_mse = sur.fit(epochs, 1e-3, restandardise=True)
     t_train = time.time() - t1
-    theta0 = rng.uniform(-np.pi, np.pi, P)
-    plain = MPSEnergy(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"], "c128", 641)
-    hp, bp = plain_adam(plain, theta0, a.lr, a.budget)
-    verifier = MPSEnergy(wl["n"], wl["chi_max"], wl["eps"], wl["circuit"], P, wl["terms"], "c128", 641)
-    hs, bs, st = surrogate_adam(verifier, sur, theta0, a.lr, a.budget)
-    e_star = min(bp[0], bs[0])
-    target = e_star + 1e-4
-    out = {"workload": "heis40: n=40, 4 layers Ry/Rz + CNOT ladder (320 params), chi 64, "
-                       "cutoff 1e-10, Heisenberg 157 terms",
-           "n_data": a.n_data, "data_s": t_data, "train_s": t_train, "train_mse": train_mse,
-           "E0": float(plain(theta0[None])[0]), "E_star": e_star, "target": target,
-           "plain_best": bp[0], "surrogate_best": bs[0],
-           "plain_evals_to_target": evals_to(hp, target),
-           "surrogate_evals_to_target": evals_to(hs, target),
-           "surrogate_evals_to_plain_best": evals_to(hs, bp[0]),
-           "plain_evals_to_plain_best": evals_to(hp, bp[0]),
-           "plain_evals": hp[-1][0], "surrogate_evals": hs[-1][0], "surrogate_stats": st}
+    pre = sur.net.get_params().clone()
+    mu, sd = sur.mu, sur.sd
+    energy = MPSEnergy(*args, dtype, 2 * P + 1, small=1)
+    judge = MPSEnergy(*args, "c128", 8)
+    rows = []
+    for k in range(starts):
+        t2 = time.time()
+        theta0 = np.random.default_rng(5000 + 100 * seed + k).uniform(-np.pi, np.pi, P)
+        refs = []
+        for lr_r in ref_lrs:
+            energy.evals = 0
+            _, b = plain_adam(energy, theta0, lr_r, ref_budget)
+            refs.append(b)
+        e_star_run = min(b[0] for b in refs)
+        best_ref = min(refs, key=lambda b: b[0])
+        e_star = float(judge(best_ref[1][None])[0])
+        # both compared runs are judged in the optimisers' own form
+        target = e_star_run + 1e-4
+        energy.evals = 0
+        hp, bp = plain_adam(energy, theta0, lr, budget)
+        sur.net.set_params(pre)
+        sur.mu, sur.sd = mu, sd
+        sur.X, sur.Y = X.copy(), Y.copy()
+        energy.evals = 0
+        hs, bs, st = surrogate_adam(energy, sur, theta0, lr, budget, rng=np.random.default_rng(k))
+        row = {"start": k, "E0": float(judge(theta0[None])[0]), "E_star": e_star,
+               "E_star_optimiser_form": e_star_run,
+               "reference_bests": [float(b[0]) for b in refs],
+               "plain_best": float(bp[0]), "surrogate_best": float(bs[0]),
+               "plain_best_c128": float(judge(bp[1][None])[0]),
+               "surrogate_best_c128": float(judge(np.asarray(bs[1])[None])[0]),
+               "plain_evals_to_target": evals_to(hp, target),
+               "surrogate_evals_to_target": evals_to(hs, target),
+               "plain_evals_to_plain_best": evals_to(hp, bp[0]),
+               "surrogate_evals_to_plain_best": evals_to(hs, bp[0]),
+               "surrogate_stats": st, "seconds": time.time() - t2}
+        rows.append(row)
+        if log:
+            log(json.dumps(row))
+    return {"workload": wl["name"], "params": P, "budget": budget, "lr": lr, "form": dtype,
+            "reference": {"learning_rates": list(ref_lrs), "budget": ref_budget},
+            "n_data": n_data, "data_s": t_data, "train_s": t_train, "train_mse": train_mse,
+            "starts": rows}
+
+
+def main():
+    import argparse
+    ap = argparse.ArgumentParser(description="surrogate-assisted vs plain VQE on the MPS")
+    ap.add_argument("--workload", default="heis40")
+    ap.add_argument("--starts", type=int, default=3)
+    ap.add_argument("--n-data", type=int, default=100000)
+    ap.add_argument("--budget", type=int, default=200000)
+    ap.add_argument("--ref-budget", type=int, default=300000)
+    ap.add_argument("--lr", type=float, default=0.02)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--dtype", default="c64", choices=("c64", "c64_bf16split", "c128"))
+    a = ap.parse_args()
+    wl = inputs.workload(a.workload)
+    out = compare(wl, a.starts, a.budget, a.lr, ref_budget=a.ref_budget, n_data=a.n_data,
+                  epochs=a.epochs, seed=a.seed, dtype=a.dtype,
+                  log=lambda t: print(t, flush=True))
     print(json.dumps(out))
 
 
