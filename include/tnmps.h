@@ -295,10 +295,16 @@ tnmps_status tnmps_get_stats(tnmps_ctx *ctx, tnmps_stats *out);
  *   gemm_stages: shared-memory ring depth of the tensor-core GEMMs of the
  *     BF16-split form (two-site block, split, sweeps): 0 (default) = as many
  *     as fit, at most 3; or 2 or 3 (capped at what fits).
+ *   sweep_fused: transfer sweeps of the BF16-split form: 0 (default) = each
+ *     trie level as two launches (all step-1 products, then all step-2
+ *     products, the intermediates in the workspace); 1 = one launch per level
+ *     whose CTAs run both steps of their own (state, node) updates, the
+ *     intermediates in two slots per CTA that stay in L2.
  * TNMPS_ERR_ARG on any other value. */
 typedef struct {
   int32_t jacobi_shape[3];
   int32_t gemm_stages;
+  int32_t sweep_fused;
 } tnmps_tuning;
 tnmps_status tnmps_set_tuning(tnmps_ctx *ctx, const tnmps_tuning *tuning);
 tnmps_status tnmps_get_tuning(const tnmps_ctx *ctx, tnmps_tuning *tuning);

@@ -8,6 +8,8 @@ Knobs (``tnmps_tuning`` in include/tnmps.h, plus the expectation chunk):
   blocks, or one CTA of 512 threads per SM with 32-column blocks);
 * ``gemm_stages`` -- shared-memory ring depth (2 or 3) of the tensor-core
   GEMMs of the BF16-split form (two-site block, split, transfer sweeps);
+* ``sweep_fused`` -- the transfer sweeps of the BF16-split form as two
+  launches per trie level or as one launch running both steps per CTA;
 * ``chunk`` -- states per expectation chunk of each term set (the workspace
   size: a wider chunk fills more SMs per trie level, a narrower one keeps the
   environments in L2).
@@ -28,7 +30,7 @@ import torch
 
 from . import tnmps
 
-DEFAULT = {"jacobi_shape": [0, 0, 0], "gemm_stages": 0}
+DEFAULT = {"jacobi_shape": [0, 0, 0], "gemm_stages": 0, "sweep_fused": 0}
 
 
 def cache_path():
@@ -104,7 +106,7 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
         torch.cuda.synchronize(m.device)
         return min(_time(circuit, stream), _time(circuit, stream))
 
-    cfg = {"jacobi_shape": list(DEFAULT["jacobi_shape"]), "gemm_stages": DEFAULT["gemm_stages"]}
+    cfg = json.loads(json.dumps(DEFAULT))
     trials = []
     best_t = circuit_time(cfg)
     default_circuit = best_t
@@ -144,6 +146,25 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
         passes[name] = {"candidates_s": {str(k): v for k, v in res.items()},
                         "default_chunk": 0 if 0 in res else int(min(res)),
                         "best_s": res[best]}
+    # the sweep form, on the sum of the term sets' passes at their chunks
+    if m.dtype == "c64_bf16split" and passes:
+        def passes_time():
+            tot = 0.0
+            for name, ps in term_sets.items():
+                m.expect_dev(ps, energy, chunk=chunks[name])
+                torch.cuda.synchronize(m.device)
+                tot += _time(lambda: m.expect_dev(ps, energy, chunk=chunks[name]), stream)
+            m._ws = {}
+            return tot
+        base = passes_time()
+        alt = json.loads(json.dumps(cfg))
+        alt["sweep_fused"] = 1
+        m.set_tuning(**alt)
+        t_alt = passes_time()
+        trials.append({"tuning": alt, "expect_passes_s": t_alt, "versus": base})
+        if t_alt < base:
+            cfg = alt
+        m.set_tuning(**cfg)
     rep = {"tuning": cfg, "chunk": chunks, "circuit_s": {"default": default_circuit,
                                                           "tuned": best_t},
            "expect_s": passes, "trials": trials, "cached": False,

@@ -1327,6 +1327,8 @@ tnmps_status tnmps_set_tuning(tnmps_ctx *c, const tnmps_tuning *t) {
       return fail(c, TNMPS_ERR_ARG, "jacobi_shape must be 0 or 1");
   if (t->gemm_stages != 0 && t->gemm_stages != 2 && t->gemm_stages != 3)
     return fail(c, TNMPS_ERR_ARG, "gemm_stages must be 0, 2 or 3");
+  if (t->sweep_fused != 0 && t->sweep_fused != 1)
+    return fail(c, TNMPS_ERR_ARG, "sweep_fused must be 0 or 1");
   c->tuning = *t;
   return TNMPS_OK;
 }

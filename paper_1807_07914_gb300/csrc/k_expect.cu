@@ -350,6 +350,8 @@ static cudaError_t run_levels_tc(tnmps_ctx *c, const TermPlan &p, const WsLayout
   cudaStream_t st = c->stream;
   TcSweep t{};
   t.stages = c->tuning.gemm_stages;
+  t.fused = c->tuning.sweep_fused;
+  t.tslots = (int64_t)((L.total - L.tmp_off) / (2 * (size_t)L.tc_env_bytes));
   t.dims = c->dims;
   t.n = c->n;
   t.b0 = e.b0;

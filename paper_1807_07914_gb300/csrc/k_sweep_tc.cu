@@ -232,6 +232,239 @@ struct Step2 {
   }
 };
 
+// ------------------------------------------------------------ fused level
+// Both steps of a trie level in one persistent launch. CTA c takes the
+// (state, node) units c, c + G, c + 2G, ... (G CTAs) and runs, for its k-th
+// unit, the step-1 M tiles of unit k and then the step-2 M tiles of unit
+// k - 1: step 2 of a unit starts one unit later, while step 1 of the next
+// unit keeps the tensor pipe busy. The unit's intermediate T goes to one of
+// two T slots of the CTA (slot k & 1) instead of a per-unit buffer, so it is
+// written and read back by the same SM within about one unit's time and
+// stays in L2. The hand-off: the epilogue warps store T (generic proxy),
+// fence it for the async proxy and arrive on the slot's mbarrier; the
+// producer waits on it before its bulk copies read T. A slot is rewritten
+// two units later, after the MMAs that read it have completed (their
+// completion precedes the accumulator that the rewriting epilogue waits for).
+// Roles and bounded waits as in ctc::k_cgemm.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+struct FusedItem {
+  int unit, step, g, k;  // step 1 or 2; k: index of the unit in this CTA's sequence
+};
+
+// calls f(item) for this CTA's item sequence in order; f returns false to stop
+template <class F>
+__device__ __forceinline__ void for_items(int units, int grid_m1, int grid_m2, F f) {
+  const int G = gridDim.x, c = blockIdx.x;
+  const int K = c < units ? (units - c + G - 1) / G : 0;
+  for (int k = 0; k <= K; ++k) {
+    if (k < K)
+      for (int g = 0; g < grid_m1; ++g)
+        if (!f(FusedItem{c + k * G, 1, g, k})) return;
+    if (k >= 1)
+      for (int g = 0; g < grid_m2; ++g)
+        if (!f(FusedItem{c + (k - 1) * G, 2, g, k - 1})) return;
+  }
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(192, 1) k_sweep_fused(Step1 p1, Step2 p2, int units,
+                                                        uint32_t *err) {
+  constexpr int P = 2;
+  using RG = ctc::Ring<NMAX, 0, P, 3>;
+  constexpr int S = RG::S;
+  extern __shared__ uint8_t smraw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
+                                            ~(uintptr_t)1023);
+  __shared__ uint64_t full[S], empty[S], acc_full[2], acc_empty[2], mma_done, t_ready[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t NTM = 2 * NMAX;
+  const int gm1 = p1.lv.grid_m, gm2 = p2.lv.grid_m;
+  const TcSweep &t = p1.t;
+  auto setup = [&](const FusedItem &it, Unit &u) {
+    bool ok;
+    if (it.step == 1) {
+      ok = p1.setup(it.unit * gm1 + it.g, u);
+      if (ok)  // T half s' of the slot (setup put it in the per-unit buffer)
+        u.out = t.tbuf + ((int64_t)(blockIdx.x * 2 + (it.k & 1)) * 2 +
+                          (u.out - t.tbuf) / t.env_bytes % 2) * t.env_bytes;
+    } else {
+      ok = p2.setup(it.unit * gm2 + it.g, u);
+      if (ok) u.b = t.tbuf + (int64_t)(blockIdx.x * 2 + (it.k & 1)) * 2 * t.env_bytes;
+    }
+    return ok;
+  };
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, NTM);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 32) {
+    for (int q = 0; q < S; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 4);
+      tc::mbar_init(&t_ready[b], 4);
+    }
+    tc::mbar_init(&mma_done, 1);
+    tc::mbar_fence_init();
+    s_fail = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int *fail = &s_fail;
+
+  if (warp == 4) {
+    if (lane == 0) {  // producer
+      int kg = 0;
+      int waited = -1;  // last unit index whose T hand-off was awaited
+      for_items(units, gm1, gm2, [&](const FusedItem &it) {
+        if (*fail) return false;
+        Unit u;
+        if (!setup(it, u)) return true;
+        if (it.step == 2 && it.k != waited) {
+          if (!ctc::wait_or_fail(&t_ready[it.k & 1], (uint32_t)((it.k >> 1) & 1), fail))
+            return false;
+          waited = it.k;
+        }
+        for (int kt = 0; kt < u.nk; ++kt, ++kg) {
+          const int q = kg % S;
+          if (kg >= S && !ctc::wait_or_fail(&empty[q], (uint32_t)(((kg / S) - 1) & 1), fail))
+            return false;
+          const int sh = kt / u.kc, qq = kt - sh * u.kc;
+          const uint8_t *a = u.a + sh * u.a_s + qq * u.a_kt;
+          const uint8_t *b = u.b + sh * u.b_s + qq * u.b_kt;
+          uint8_t *st = sm + q * RG::STAGE;
+          tc::mbar_arrive_expect_tx(&full[q], P * (RG::A_PIECE + u.b_bytes));
+#pragma unroll
+          for (int pc = 0; pc < P; ++pc) {
+            tc::bulk_g2s(st + pc * RG::A_PIECE, a + pc * u.a_pc, RG::A_PIECE, &full[q]);
+            tc::bulk_g2s(st + P * RG::A_PIECE + pc * RG::B_PIECE, b + pc * u.b_pc, u.b_bytes,
+                         &full[q]);
+          }
+        }
+        return true;
+      });
+      for (int k = kg > S ? kg - S : 0; k < kg; ++k)
+        if (!tc::mbar_wait(&full[k % S], (uint32_t)((k / S) & 1))) s_fail = 1;
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    if (lane == 0) {  // MMA issuer
+      int kg = 0, n = 0;
+      for_items(units, gm1, gm2, [&](const FusedItem &it) {
+        if (*fail) return false;
+        Unit u;
+        if (!setup(it, u)) return true;
+        const int ab = n & 1;
+        if (n >= 2 && !ctc::wait_or_fail(&acc_empty[ab], (uint32_t)(((n >> 1) - 1) & 1), fail))
+          return false;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(ab * NMAX);
+        const uint32_t idesc = tc::idesc_bf16(128, u.N);
+        for (int kt = 0; kt < u.nk; ++kt, ++kg) {
+          const int q = kg % S;
+          if (!ctc::wait_or_fail(&full[q], (uint32_t)((kg / S) & 1), fail)) return false;
+          tc::fence_after_sync();
+          const uint32_t a = tc::smem_u32(sm + q * RG::STAGE);
+          const uint32_t b = a + P * RG::A_PIECE;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int o = 0; o < P; ++o)
+#pragma unroll
+              for (int pa = 0; pa <= o; ++pa) {
+                const uint64_t ad = tc::smem_desc(a + pa * RG::A_PIECE + j * 256, 128, 1024);
+                const uint64_t bd =
+                    tc::smem_desc(b + (o - pa) * RG::B_PIECE + j * 256, 128, 1024);
+                tc::mma_bf16(d, ad, bd, idesc, (kt > 0 || j > 0 || o > 0) ? 1u : 0u);
+              }
+          tc::mma_commit(&empty[q]);
+        }
+        tc::mma_commit(&acc_full[ab]);
+        if (it.step == 2) p2.done(u);
+        ++n;
+        return true;
+      });
+      tc::mma_commit(&mma_done);
+      if (!tc::mbar_wait(&mma_done, 0)) s_fail = 1;
+    }
+    __syncwarp();
+  } else {  // epilogue warps 0-3
+    int n = 0;
+    for_items(units, gm1, gm2, [&](const FusedItem &it) {
+      if (*fail) return false;
+      Unit u;
+      if (setup(it, u)) {
+        const int ab = n & 1;
+        if (!ctc::wait_or_fail(&acc_full[ab], (uint32_t)((n >> 1) & 1), fail)) return false;
+        tc::fence_after_sync();
+        const uint32_t src = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * NMAX);
+        for (int c = 0; c < u.N; c += 32) {
+          float v[32];
+          tc::tmem_ld32(src + (uint32_t)c, v);
+          rowk_epi(u, warp, lane, c, v, t.rt);
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                           tc::smem_u32(&acc_empty[ab]))
+                       : "memory");
+        ++n;
+      }
+      // after the unit's last step-1 tile: hand T over to the producer
+      if (it.step == 1 && it.g == gm1 - 1) {
+        fence_proxy_async_global();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                           tc::smem_u32(&t_ready[it.k & 1]))
+                       : "memory");
+      }
+      return true;
+    });
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0) atomicOr(err, TNMPS_EFLAG_TIMEOUT);
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, NTM);
+}
+
+template <int NMAX>
+cudaError_t launch_fused(const Step1 &p1, const Step2 &p2, int units, uint32_t *err,
+                         cudaStream_t s, uint64_t *launches) {
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n_sm <= 0)
+      n_sm = 1;
+  }
+  constexpr int SMEM = ctc::Ring<NMAX, 0, 2, 3>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<NMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  if (e != cudaSuccess) return e;
+  // two T slots per CTA, each of two halves, inside the workspace's T region
+  int grid = n_sm < units ? n_sm : units;
+  const int64_t slot_cap = p1.t.tslots / 2;
+  if (grid > slot_cap) grid = (int)slot_cap;
+  if (grid < 1) return cudaErrorInvalidValue;
+  k_sweep_fused<NMAX><<<grid, 192, SMEM, s>>>(p1, p2, units, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
 // <P_t> = Re sum_{c,c'} L[c][c'] R[c][c'], L from the split row-K environment
 __global__ void __launch_bounds__(256) k_term_dot_tc(TcSweep t, const cx<float> *renv,
                                                      const int64_t *roff, int64_t renv_elems,
@@ -299,6 +532,13 @@ cudaError_t tc_level(const TcSweep &t, const int32_t *node_site, const int32_t *
   const int units = nodes * t.nb;
   cudaError_t e;
   Step1 p1{t, lv};
+  if (t.fused) {  // both steps in one launch, T kept in per-CTA slots
+    LevelArgsTc lv2 = lv;
+    lv2.grid_m = mt;
+    Step2 p2{t, lv2};
+    return t.nmax <= 128 ? launch_fused<128>(p1, p2, units, t.err, s, launches)
+                         : launch_fused<256>(p1, p2, units, t.err, s, launches);
+  }
   e = t.nmax <= 128
           ? ctc::launch_cgemm<Step1, 128>(p1, (int64_t)units * lv.grid_m, t.err, s, launches,
                                           t.stages)

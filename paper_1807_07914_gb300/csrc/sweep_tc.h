@@ -43,6 +43,8 @@ struct TcSweep {
   int rt;                   // row tiles of an environment (ceil(chi/128))
   int nmax;                 // 128 or 256: widest MMA N (>= every bond dimension)
   int stages;               // GEMM ring depth request (0: as many as fit)
+  int fused;                // 1: both steps of a level in one launch (k_sweep_fused)
+  int64_t tslots;           // (state, node) T buffers in tbuf (each 2 x env_bytes)
   uint32_t *err;
 };
 

@@ -9,7 +9,8 @@ shape of a saturated chi=128 two-site block) ``--reps`` times; ``circuit``
 runs the chi=128 ansatz on a reduced batch and then the Heisenberg energy;
 ``sweep`` builds the chi=128 states (7 layers saturate the middle bonds) and
 then evaluates the first ``--terms`` of the 2000 random strings ``--reps``
-times (one state chunk). All exit non-zero on any library error.
+times (one state chunk; ``--sweep-fused 1`` runs both steps of a trie level in
+one launch). All exit non-zero on any library error.
 """
 import argparse
 import os
@@ -57,6 +58,7 @@ def sweep(a):
     m = tnmps.MPSBatch(40, 128, a.batch, dtype=a.dtype, max_params=P, eps=wl["eps"])
     th = inputs.thetas(a.batch, P, inputs.rng_for(5, 7))
     m.apply_circuit(circ, th)
+    m.set_tuning(sweep_fused=a.sweep_fused)
     ps = tnmps.PauliSum(40, wl["terms_random"][:a.terms])
     energy = torch.empty(a.batch, dtype=torch.float64, device="cuda")
     for _ in range(a.reps):
@@ -77,6 +79,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--layers", type=int, default=9)
+    ap.add_argument("--sweep-fused", type=int, default=0,
+                    help="sweep: both steps of a trie level in one launch (tnmps_tuning)")
     a = ap.parse_args()
     {"jacobi": jacobi, "circuit": circuit, "sweep": sweep}[a.case](a)
 

@@ -40,7 +40,8 @@ class Job(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("jacobi_shape", C.c_int32 * 3), ("gemm_stages", C.c_int32)]
+    _fields_ = [("jacobi_shape", C.c_int32 * 3), ("gemm_stages", C.c_int32),
+                ("sweep_fused", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -438,19 +439,21 @@ class MPSBatch:
         self._check(lib().tnmps_profile_read(self._h, _ptr(ms), _ptr(cnt)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
 
-    def set_tuning(self, jacobi_shape=(0, 0, 0), gemm_stages=0):
+    def set_tuning(self, jacobi_shape=(0, 0, 0), gemm_stages=0, sweep_fused=0):
         """Launch shapes of the context's kernels (see tnmps_tuning in
         include/tnmps.h); the results do not depend on them."""
         t = Tuning()
         for i, v in enumerate(jacobi_shape):
             t.jacobi_shape[i] = int(v)
         t.gemm_stages = int(gemm_stages)
+        t.sweep_fused = int(sweep_fused)
         self._check(lib().tnmps_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self):
         t = Tuning()
         self._check(lib().tnmps_get_tuning(self._h, C.byref(t)))
-        return {"jacobi_shape": [int(v) for v in t.jacobi_shape], "gemm_stages": int(t.gemm_stages)}
+        return {"jacobi_shape": [int(v) for v in t.jacobi_shape], "gemm_stages": int(t.gemm_stages),
+                "sweep_fused": int(t.sweep_fused)}
 
     def inject(self, nth, status):
         self._check(lib().tnmps_debug_inject(self._h, int(nth), int(status)))

@@ -19,12 +19,12 @@ if not torch.cuda.is_available():
 from paper_1807_07914_gb300 import autotune, tnmps  # noqa: E402
 
 CANDIDATES = [
-    {"jacobi_shape": [0, 0, 0], "gemm_stages": 0},
-    {"jacobi_shape": [1, 0, 0], "gemm_stages": 0},
-    {"jacobi_shape": [0, 1, 0], "gemm_stages": 0},
-    {"jacobi_shape": [0, 0, 1], "gemm_stages": 0},
-    {"jacobi_shape": [1, 1, 1], "gemm_stages": 2},
-    {"jacobi_shape": [0, 0, 0], "gemm_stages": 3},
+    {"jacobi_shape": [0, 0, 0], "gemm_stages": 0, "sweep_fused": 0},
+    {"jacobi_shape": [1, 0, 0], "gemm_stages": 0, "sweep_fused": 0},
+    {"jacobi_shape": [0, 1, 0], "gemm_stages": 0, "sweep_fused": 0},
+    {"jacobi_shape": [0, 0, 1], "gemm_stages": 0, "sweep_fused": 0},
+    {"jacobi_shape": [1, 1, 1], "gemm_stages": 2, "sweep_fused": 1},
+    {"jacobi_shape": [0, 0, 0], "gemm_stages": 3, "sweep_fused": 1},
 ]
 
 
@@ -63,11 +63,32 @@ def test_every_candidate_matches_oracle(reference, dtype, cand):
 
 def test_bad_tuning_rejected():
     m = tnmps.MPSBatch(4, 4, 1, dtype="c64")
-    for bad in ({"jacobi_shape": [2, 0, 0]}, {"gemm_stages": 1}, {"gemm_stages": 4}):
+    for bad in ({"jacobi_shape": [2, 0, 0]}, {"gemm_stages": 1}, {"gemm_stages": 4},
+                {"sweep_fused": 2}):
         with pytest.raises(tnmps.TnmpsError) as ei:
             m.set_tuning(**bad)
         assert ei.value.status == 1
-    assert m.get_tuning() == {"jacobi_shape": [0, 0, 0], "gemm_stages": 0}
+    assert m.get_tuning() == {"jacobi_shape": [0, 0, 0], "gemm_stages": 0, "sweep_fused": 0}
+
+
+@pytest.mark.parametrize("chunk", [0, 3])
+def test_fused_sweep_bit_identical_to_two_launches(chunk):
+    """Both steps of each trie level in one launch (T in per-CTA slots) give
+    exactly the two-launch values: the same MMAs and epilogues, only the
+    launch structure and the T buffers differ. 5 states of 9-layer 40-qubit
+    states (middle bonds at 128), 400 random strings, ragged state chunks."""
+    wl = inputs.workload("chi128")
+    circ, P = inputs.hea_circuit(40, 9, ("RY", "RZ"))
+    th = inputs.thetas(5, P, np.random.default_rng(9))
+    m = tnmps.MPSBatch(40, 128, 5, dtype="c64_bf16split", max_params=P, eps=1e-10)
+    m.apply_circuit(circ, th)
+    ps = tnmps.PauliSum(40, wl["terms_random"][:400])
+    out = []
+    for fused in (0, 1):
+        m.set_tuning(sweep_fused=fused)
+        out.append(m.expect(ps, per_term=True, chunk=chunk))
+        m.check()
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][0], out[1][0])
 
 
 def test_tuner_picks_a_candidate_and_keeps_results(tmp_path, monkeypatch):
@@ -81,7 +102,8 @@ def test_tuner_picks_a_candidate_and_keeps_results(tmp_path, monkeypatch):
     ps = tnmps.PauliSum(wl["n"], wl["terms"])
     rep = autotune.tune_context(m, gates_c, th, {"heis": ps}, chunk_candidates=(2, 4))
     assert not rep["cached"] and m.get_tuning() == rep["tuning"]
-    assert rep["circuit_s"]["tuned"] <= min(t["circuit_s"] for t in rep["trials"]) + 1e-12
+    assert rep["circuit_s"]["tuned"] <= min(t["circuit_s"] for t in rep["trials"]
+                                            if "circuit_s" in t) + 1e-12
     assert rep["chunk"]["heis"] in (0, 2, 4)
     again = autotune.tune_context(m, gates_c, th, {"heis": ps})
     assert again["cached"] and again["tuning"] == rep["tuning"]
