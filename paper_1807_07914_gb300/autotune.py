@@ -28,8 +28,6 @@ import os
 
 import torch
 
-from . import tnmps
-
 DEFAULT = {"jacobi_shape": [0, 0, 0], "gemm_stages": 0, "sweep_fused": 0}
 
 
@@ -41,7 +39,7 @@ def cache_path():
 
 def _key(m, term_sets):
     h = hashlib.sha1()
-    h.update(str(torch.cuda.get_device_name(m.device)).encode())
+    h.update(str(m.device_name()).encode())
     h.update(repr((m.n, m.chi, m.dtype, m.batch)).encode())
     for name, ps in term_sets.items():
         h.update(repr((name, ps.n_terms, ps.info()["max_level_nodes"])).encode())
@@ -65,22 +63,35 @@ def _store(table):
         pass
 
 
-def _time(fn, stream, reps=1):
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
+class CudaTimer:
+    """Seconds of ``fn`` by CUDA events on the context's current stream."""
+
+    def __init__(self, device):
+        self.device = device
+        self.stream = torch.cuda.current_stream(device)
+
+    def sync(self):
+        torch.cuda.synchronize(self.device)
+
+    def __call__(self, fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
         fn()
-    e1.record(stream)
-    torch.cuda.synchronize(stream.device)
-    return e0.elapsed_time(e1) / 1000.0 / reps
+        e1.record(self.stream)
+        torch.cuda.synchronize(self.device)
+        return e0.elapsed_time(e1) / 1000.0
 
 
 def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32, 64),
-                 max_workspace_bytes=40 << 30, use_cache=True):
+                 max_workspace_bytes=40 << 30, use_cache=True, timer=None, energy=None):
     """Tune the context ``m`` for the circuit (``gates_c`` from gate_array,
     ``thetas_dev`` [batch, n_params] on the device) and the named term sets
     (``{name: PauliSum}``). Leaves the best launch shapes set on ``m``.
+
+    ``timer`` (default: CUDA events on the context's stream) times a callable
+    and ``timer.sync()`` waits for the device; ``energy`` is the device output
+    buffer of the trial passes (default: a new one).
 
     Returns a report: the chosen ``tuning`` and ``chunk`` per term set, the
     seconds of the circuit and of each term set's pass with the defaults and
@@ -93,8 +104,9 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
         m.set_tuning(**rep["tuning"])
         rep["cached"] = True
         return rep
-    stream = torch.cuda.current_stream(m.device)
-    energy = torch.empty(m.batch, dtype=torch.float64, device=m.device)
+    timer = timer or CudaTimer(m.device)
+    if energy is None:
+        energy = torch.empty(m.batch, dtype=torch.float64, device=m.device)
 
     def circuit():
         m.reset()
@@ -103,8 +115,8 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
     def circuit_time(cfg):
         m.set_tuning(**cfg)
         circuit()                    # first pass loads the kernels of this shape
-        torch.cuda.synchronize(m.device)
-        return min(_time(circuit, stream), _time(circuit, stream))
+        timer.sync()
+        return min(timer(circuit), timer(circuit))
 
     cfg = json.loads(json.dumps(DEFAULT))
     trials = []
@@ -128,19 +140,19 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
             best_t, cfg = t, cand
     m.set_tuning(**cfg)
     circuit()
-    torch.cuda.synchronize(m.device)
+    timer.sync()
     # states per expectation chunk, per term set (on the circuit's final states)
     chunks, passes = {}, {}
     for name, ps in term_sets.items():
         res = {}
         for ch in (0,) + tuple(c for c in chunk_candidates if c < m.batch):
-            nb = tnmps.lib().tnmps_expect_workspace_bytes(m._h, ps._h, int(ch))
+            nb = m.workspace_bytes(ps, ch)
             if nb == 0 or nb > max_workspace_bytes:
                 continue
             m.expect_dev(ps, energy, chunk=ch)       # workspace, plan upload
-            torch.cuda.synchronize(m.device)
-            res[ch] = _time(lambda: m.expect_dev(ps, energy, chunk=ch), stream)
-        m._ws = {}                                   # free the trial workspaces
+            timer.sync()
+            res[ch] = timer(lambda: m.expect_dev(ps, energy, chunk=ch))
+        m.drop_workspaces()
         best = min(res, key=res.get)
         chunks[name] = int(best)
         passes[name] = {"candidates_s": {str(k): v for k, v in res.items()},
@@ -152,9 +164,9 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
             tot = 0.0
             for name, ps in term_sets.items():
                 m.expect_dev(ps, energy, chunk=chunks[name])
-                torch.cuda.synchronize(m.device)
-                tot += _time(lambda: m.expect_dev(ps, energy, chunk=chunks[name]), stream)
-            m._ws = {}
+                timer.sync()
+                tot += timer(lambda: m.expect_dev(ps, energy, chunk=chunks[name]))
+            m.drop_workspaces()
             return tot
         base = passes_time()
         alt = json.loads(json.dumps(cfg))

@@ -333,6 +333,18 @@ class MPSBatch:
             self._ws = {key: ws}
         return ws
 
+    def device_name(self):
+        return torch.cuda.get_device_name(self.device)
+
+    def workspace_bytes(self, terms, chunk=0):
+        """Device bytes of an expectation workspace for ``chunk`` states at a
+        time (0: the whole batch); 0 on a mismatch."""
+        return int(lib().tnmps_expect_workspace_bytes(self._h, terms._h, int(chunk)))
+
+    def drop_workspaces(self):
+        """Release the cached expectation workspace (PyTorch memory)."""
+        self._ws = {}
+
     def expect(self, terms, per_term=False, chunk=0):
         """Energies [batch] (and Re<P_k> [batch, T]) as numpy, synchronous."""
         ws = self.workspace(terms, chunk)
