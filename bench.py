@@ -51,7 +51,7 @@ def load_peaks():
         return {}
 
 
-def profiled_traffic(name):
+def profiled_traffic(name, key="traffic_bytes"):
     """DRAM bytes (read + write) of a kernel from its committed ncu summary in
     profiles/: the figures of its machine-readable lines, kept only while the
     sha256 of the kernel's sources equals the one recorded with the capture
@@ -65,10 +65,10 @@ def profiled_traffic(name):
     kv = {}
     for ln in lines:
         if ":" in ln and ln.split(":", 1)[0].strip() in (
-                "traffic_bytes", "traffic_unit", "sources", "sources_sha256"):
+                key, "traffic_unit", "sources", "sources_sha256"):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if not {"traffic_bytes", "sources", "sources_sha256"} <= kv.keys():
+    if not {key, "sources", "sources_sha256"} <= kv.keys():
         return None
     h = hashlib.sha256()
     for src in kv["sources"].split():
@@ -78,7 +78,7 @@ def profiled_traffic(name):
             return None
     if h.hexdigest() != kv["sources_sha256"]:
         return None
-    return {"bytes": float(kv["traffic_bytes"]), "unit": kv.get("traffic_unit", "per launch"),
+    return {"bytes": float(kv[key]), "unit": kv.get("traffic_unit", "per launch"),
             "source": "profiles/" + name}
 
 
@@ -311,7 +311,10 @@ def random_terms_pass(args, m, wl, energy, stream, ws, device, chunk):
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
             "note": "achieved = algorithmic complex-GEMM flops (4 real MACs per complex MAC); "
                     "executed = 3 x (hi*hi + hi*lo + lo*hi), padding to 32-wide tiles not counted"}
-        tr = profiled_traffic("k_swtc_bf16split_chi128_8states.md")
+        fused = m.get_tuning()["sweep_fused"] == 1
+        tr = profiled_traffic("k_swtc_bf16split_chi128_8states.md",
+                              "traffic_bytes_fused" if fused else "traffic_bytes")
+        out["sweep_form"] = "fused (k_sweep_fused)" if fused else "two launches per level"
         if tr is not None:
             upd = out["env_updates"]
             out["roofline"]["traffic"] = tr["bytes"] * upd

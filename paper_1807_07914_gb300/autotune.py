@@ -84,14 +84,17 @@ class CudaTimer:
 
 
 def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32, 64),
-                 max_workspace_bytes=40 << 30, use_cache=True, timer=None, energy=None):
+                 max_workspace_bytes=40 << 30, use_cache=True, timer=None, energy=None,
+                 margin=0.01):
     """Tune the context ``m`` for the circuit (``gates_c`` from gate_array,
     ``thetas_dev`` [batch, n_params] on the device) and the named term sets
     (``{name: PauliSum}``). Leaves the best launch shapes set on ``m``.
 
     ``timer`` (default: CUDA events on the context's stream) times a callable
     and ``timer.sync()`` waits for the device; ``energy`` is the device output
-    buffer of the trial passes (default: a new one).
+    buffer of the trial passes (default: a new one). A candidate replaces the
+    current choice only when it is faster by more than ``margin`` (relative),
+    so that timing noise does not move a knob away from its default.
 
     Returns a report: the chosen ``tuning`` and ``chunk`` per term set, the
     seconds of the circuit and of each term set's pass with the defaults and
@@ -136,7 +139,7 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
             cand[name][idx] = val
         t = circuit_time(cand)
         trials.append({"tuning": cand, "circuit_s": t})
-        if t < best_t:
+        if t < (1 - margin) * best_t:
             best_t, cfg = t, cand
     m.set_tuning(**cfg)
     circuit()
@@ -151,9 +154,12 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
                 continue
             m.expect_dev(ps, energy, chunk=ch)       # workspace, plan upload
             timer.sync()
-            res[ch] = timer(lambda: m.expect_dev(ps, energy, chunk=ch))
+            res[ch] = min(timer(lambda: m.expect_dev(ps, energy, chunk=ch)) for _ in range(2))
         m.drop_workspaces()
         best = min(res, key=res.get)
+        first = 0 if 0 in res else min(res)           # the whole batch when it fits
+        if not res[best] < (1 - margin) * res[first]:
+            best = first
         chunks[name] = int(best)
         passes[name] = {"candidates_s": {str(k): v for k, v in res.items()},
                         "default_chunk": 0 if 0 in res else int(min(res)),
@@ -165,7 +171,8 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
             for name, ps in term_sets.items():
                 m.expect_dev(ps, energy, chunk=chunks[name])
                 timer.sync()
-                tot += timer(lambda: m.expect_dev(ps, energy, chunk=chunks[name]))
+                tot += min(timer(lambda: m.expect_dev(ps, energy, chunk=chunks[name]))
+                           for _ in range(2))
             m.drop_workspaces()
             return tot
         base = passes_time()
@@ -174,7 +181,7 @@ def tune_context(m, gates_c, thetas_dev, term_sets, chunk_candidates=(8, 16, 32,
         m.set_tuning(**alt)
         t_alt = passes_time()
         trials.append({"tuning": alt, "expect_passes_s": t_alt, "versus": base})
-        if t_alt < base:
+        if t_alt < (1 - margin) * base:
             cfg = alt
         m.set_tuning(**cfg)
     rep = {"tuning": cfg, "chunk": chunks, "circuit_s": {"default": default_circuit,
