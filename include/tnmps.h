@@ -36,9 +36,10 @@
  *   - Every call returns a tnmps_status; no call aborts, exits or traps.
  *     tnmps_last_error(ctx) describes the last failure. Device-side problems
  *     (an SVD that did not converge within its sweep cap, NaN/Inf in the
- *     state) are recorded in a device flag and reported by the next
- *     synchronising call or by tnmps_check. After an error the state is
- *     unspecified until tnmps_reset.
+ *     state, a bounded wait of a tensor-core pipeline that ran out) are
+ *     recorded in a device flag and reported by the next synchronising call
+ *     or by tnmps_check. After an error the state is unspecified until
+ *     tnmps_reset, which also clears the flag; the context stays usable.
  *
  * Threading: a context is used by one host thread at a time.
  */
@@ -80,7 +81,10 @@ typedef enum {
   TNMPS_ERR_NOT_CONVERGED = 4,  /* Jacobi SVD hit its sweep cap               */
   TNMPS_ERR_NUMERIC = 5,        /* NaN or Inf met in singular values/energies */
   TNMPS_ERR_CUDA = 6,           /* a CUDA runtime call failed                 */
-  TNMPS_ERR_INJECTED = 7        /* host-side fault injection (tests only)     */
+  TNMPS_ERR_INJECTED = 7,       /* host-side fault injection (tests only)     */
+  TNMPS_ERR_TIMEOUT = 8         /* a device-side wait ran out (a tensor-core
+                                   pipeline stalled); the kernel stopped early
+                                   and flagged it, its results are invalid      */
 } tnmps_status;
 
 /* Gate opcodes (a gate list is the flat form of the paper's IR tree). */
@@ -154,6 +158,15 @@ void tnmps_free(tnmps_ctx *ctx);
  * dtype (2^-53 for TNMPS_C128, 2^-24 for TNMPS_C64): singular values at the
  * SVD's rounding-noise floor are always dropped. */
 tnmps_status tnmps_set_cutoff(tnmps_ctx *ctx, double eps);
+/* Orthogonality tolerance of the Jacobi SVD (Sec. IV's SVD): a column pair
+ * counts as orthogonal when |x^H y| <= tol * |x| |y| with
+ * tol = factor * (sqrt(rows) + 16) * u (u the dtype's unit roundoff); the
+ * iteration ends after the sweep whose largest relative rotation is below
+ * sqrt(tol) / 4. factor 1 (default) orthogonalises to the rounding level; a
+ * larger factor ends the iteration earlier (fewer sweeps) with the kept
+ * singular subspace correspondingly less exact. 1 <= factor <= 4096,
+ * TNMPS_ERR_ARG otherwise. */
+tnmps_status tnmps_set_svd_tolerance(tnmps_ctx *ctx, double factor);
 /* CUDA stream (cudaStream_t) for all work of this context; NULL = default. */
 tnmps_status tnmps_set_stream(tnmps_ctx *ctx, void *stream);
 /* Back to |0...0> with zero discarded weight and zeroed counters. */
@@ -418,7 +431,10 @@ tnmps_status tnmps_expect_pauli_sum_noalloc(tnmps_ctx *ctx, const tnmps_terms *t
  * C[M x N] = A[M x K] * B[N x K]^T with A, B given as BF16 bit patterns
  * (uint16), both K-major (row r of A at A + r*lda), C row-major FP32.
  * K, lda, ldb multiples of 8; A, B 16-byte aligned. Asynchronous on
- * `stream`. Used by the surrogate's layers; exported for unit parity. */
+ * `stream`. Used by the surrogate's layers; exported for unit parity (this
+ * entry point has no context flag: a bounded wait that runs out leaves C
+ * undefined without a report; the surrogate's own calls report it through
+ * tnmps_mlp_check). */
 tnmps_status tnmps_gemm_bf16_dev(int M, int N, int K, const uint16_t *A, int lda,
                                  const uint16_t *B, int ldb, float *C, int ldc, void *stream);
 
@@ -439,6 +455,10 @@ tnmps_status tnmps_mlp_init(tnmps_mlp **out, int d_in, int width, int max_batch,
 void tnmps_mlp_free(tnmps_mlp *mlp);
 tnmps_status tnmps_mlp_set_stream(tnmps_mlp *mlp, void *stream);
 const char *tnmps_mlp_last_error(const tnmps_mlp *mlp);
+/* Synchronise the surrogate's stream and report its device flag: a bounded
+ * wait of a tensor-core GEMM that ran out gives TNMPS_ERR_TIMEOUT (the flag
+ * is cleared; the results since the last check are invalid). */
+tnmps_status tnmps_mlp_check(tnmps_mlp *mlp);
 /* copy parameters in (also clears the Adam moments) / out */
 tnmps_status tnmps_mlp_set_params(tnmps_mlp *mlp, const float *params_dev);
 tnmps_status tnmps_mlp_get_params(tnmps_mlp *mlp, float *params_dev);
@@ -454,6 +474,15 @@ tnmps_status tnmps_mlp_backward(tnmps_mlp *mlp, const float *x_dev, const float 
  * the MSE loss of the batch. */
 tnmps_status tnmps_mlp_train_step(tnmps_mlp *mlp, const float *x_dev, const float *target_dev,
                                   int B, float lr, int step, float *loss_dev);
+
+/* Failure-detection test of the device-side waits (no paper counterpart):
+ * enqueues one kernel that waits on an mbarrier phase that nothing completes,
+ * with a limit of max_cycles SM clocks (1 <= max_cycles <= 2^31); when the
+ * wait runs out it raises the context's timeout flag and returns, exactly as
+ * a stalled tensor-core pipeline does. The next synchronising call reports
+ * TNMPS_ERR_TIMEOUT; tnmps_reset clears it. Asynchronous on the context's
+ * stream; never faults or hangs the GPU. */
+tnmps_status tnmps_debug_wait_timeout(tnmps_ctx *ctx, int64_t max_cycles);
 
 /* Host-side fault injection for error-path tests: the call number `nth`
  * (counting from 1) of any state-changing entry point returns `status`

@@ -529,6 +529,9 @@ tnmps_status sync_check(tnmps_ctx *c) {
     return fail(c, TNMPS_ERR_NUMERIC, "NaN/Inf in singular values or energies");
   if (flags & TNMPS_EFLAG_NOT_CONVERGED)
     return fail(c, TNMPS_ERR_NOT_CONVERGED, "Jacobi SVD reached its sweep cap");
+  if (flags & TNMPS_EFLAG_TIMEOUT)
+    return fail(c, TNMPS_ERR_TIMEOUT,
+                "a device-side wait ran out (tensor-core pipeline stalled); results invalid");
   return TNMPS_OK;
 }
 
@@ -594,6 +597,7 @@ const char *tnmps_status_string(tnmps_status s) {
     case TNMPS_ERR_NUMERIC: return "non-finite values";
     case TNMPS_ERR_CUDA: return "CUDA error";
     case TNMPS_ERR_INJECTED: return "injected fault";
+    case TNMPS_ERR_TIMEOUT: return "device wait timed out";
   }
   return "unknown status";
 }
@@ -1320,6 +1324,14 @@ tnmps_status tnmps_jacobi_svd_dev(tnmps_dtype dtype, int batch, int m, int n, vo
   return e == cudaSuccess ? TNMPS_OK : TNMPS_ERR_CUDA;
 }
 
+tnmps_status tnmps_set_svd_tolerance(tnmps_ctx *c, double factor) {
+  if (!c) return TNMPS_ERR_ARG;
+  if (!(factor >= 1.0 && factor <= 4096.0))
+    return fail(c, TNMPS_ERR_ARG, "tolerance factor must lie in [1, 4096]");
+  c->jacobi_tolfac = (float)factor;
+  return TNMPS_OK;
+}
+
 tnmps_status tnmps_set_tuning(tnmps_ctx *c, const tnmps_tuning *t) {
   if (!c || !t) return TNMPS_ERR_ARG;
   for (int k = 0; k < 3; ++k)
@@ -1336,6 +1348,16 @@ tnmps_status tnmps_set_tuning(tnmps_ctx *c, const tnmps_tuning *t) {
 tnmps_status tnmps_get_tuning(const tnmps_ctx *c, tnmps_tuning *t) {
   if (!c || !t) return TNMPS_ERR_ARG;
   *t = c->tuning;
+  return TNMPS_OK;
+}
+
+tnmps_status tnmps_debug_wait_timeout(tnmps_ctx *c, int64_t max_cycles) {
+  if (!c) return TNMPS_ERR_ARG;
+  if (max_cycles < 1 || max_cycles > (int64_t)1 << 31)
+    return fail(c, TNMPS_ERR_ARG, "max_cycles out of range");
+  cudaError_t e = launch_debug_wait(c->err, max_cycles, c->stream);
+  ++c->launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "debug wait");
   return TNMPS_OK;
 }
 

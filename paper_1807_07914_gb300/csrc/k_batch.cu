@@ -779,6 +779,10 @@ tnmps_status tnmps_batch_results(tnmps_batch *b, double *energy, double *discard
     b->last_error = "a Jacobi SVD reached its sweep cap";
     return TNMPS_ERR_NOT_CONVERGED;
   }
+  if (flags & TNMPS_EFLAG_TIMEOUT) {
+    b->last_error = "a device-side wait ran out";
+    return TNMPS_ERR_TIMEOUT;
+  }
   return TNMPS_OK;
 }
 

@@ -139,7 +139,7 @@ cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap) {
   a.dstride = c->n + 1;
   a.l = l;
   a.max_sweeps = c->dtype == TNMPS_C128 ? 40 : 30;
-  a.tolfac = 1.0f;
+  a.tolfac = c->jacobi_tolfac;
   a.err = c->err;
   a.counters = c->counters;
   if (c->dtype == TNMPS_C128) return dispatch<double>(a, Mcap, c->batch, c->stream);

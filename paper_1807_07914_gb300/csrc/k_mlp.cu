@@ -214,6 +214,7 @@ struct tnmps_mlp {
   float *gW1, *gb1, *gW2, *gb2, *gw3, *gb3; // views into grad
   uint16_t *W1h, *W1Th, *W2h, *W2Th, *xh, *xTh, *H1h, *H1Th, *dZ2h, *dZ2Th, *dZ1h, *dZ1Th;
   float *Z1, *Z2, *H2, *y, *dy, *sq, *dH1, *dZ2f, *dZ1f, *loss;
+  uint32_t *err;  // device flag: a GEMM's bounded wait ran out
   std::string last_error;
 };
 
@@ -236,7 +237,7 @@ std::vector<size_t> mlp_sizes(int d, int w, int maxB) {
           2 * Bp * w, 2 * Bp * w, 2 * Bp * w, 2 * Bp * w,    // dZ2h, dZ2Th, dZ1h, dZ1Th
           4 * Bp * w, 4 * Bp * w, 4 * Bp * w,                // Z1, Z2, H2
           4 * Bp, 4 * Bp, 4 * Bp,                            // y, dy, sq
-          4 * Bp * w, 4 * Bp * w, 4 * Bp * w, 256};          // dH1, dZ2f, dZ1f, loss
+          4 * Bp * w, 4 * Bp * w, 4 * Bp * w, 256, 256};     // dH1, dZ2f, dZ1f, loss, err
 }
 
 cudaError_t run_forward(tnmps_mlp *m, const float *x, int B) {
@@ -245,10 +246,10 @@ cudaError_t run_forward(tnmps_mlp *m, const float *x, int B) {
   k_x_bf16<<<592, 256, 0, s>>>(x, B, d, m->Bp, m->xh, m->xTh);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  tcg::Operands o1{m->xh, m->W1h, B, w, d, d, d, nullptr};
+  tcg::Operands o1{m->xh, m->W1h, B, w, d, d, d, m->err};
   EpiBiasSilu e1{m->b1, m->Z1, m->H1h, m->H1Th, nullptr, w, m->Bp};
   if ((e = tcg::launch(o1, e1, s)) != cudaSuccess) return e;
-  tcg::Operands o2{m->H1h, m->W2h, B, w, w, w, w, nullptr};
+  tcg::Operands o2{m->H1h, m->W2h, B, w, w, w, w, m->err};
   EpiBiasSilu e2{m->b2, m->Z2, nullptr, nullptr, m->H2, w, m->Bp};
   if ((e = tcg::launch(o2, e2, s)) != cudaSuccess) return e;
   k_last<<<(B + 7) / 8, 256, 0, s>>>(m->H2, m->w3, m->b3, B, w, m->y);
@@ -267,24 +268,24 @@ cudaError_t run_backward(tnmps_mlp *m, const float *t, int B, bool want_params, 
     k_colsum<<<w, 256, 0, s>>>(m->H2, m->dy, B, w, m->gw3);  // dw3 = H2^T dy
     k_colsum<<<1, 256, 0, s>>>(m->dy, nullptr, B, 1, m->gb3);
     k_colsum<<<w, 256, 0, s>>>(m->dZ2f, nullptr, B, w, m->gb2);
-    tcg::Operands og{m->dZ2Th, m->H1Th, w, w, Bp, Bp, Bp, nullptr};  // dW2 = dZ2^T H1
+    tcg::Operands og{m->dZ2Th, m->H1Th, w, w, Bp, Bp, Bp, m->err};  // dW2 = dZ2^T H1
     tcg::EpiStore eg{m->gW2, w, w};
     if ((e = tcg::launch(og, eg, s)) != cudaSuccess) return e;
   }
-  tcg::Operands oh{m->dZ2h, m->W2Th, B, w, w, w, w, nullptr};  // dH1 = dZ2 W2
+  tcg::Operands oh{m->dZ2h, m->W2Th, B, w, w, w, w, m->err};  // dH1 = dZ2 W2
   tcg::EpiStore eh{m->dH1, w, w};
   if ((e = tcg::launch(oh, eh, s)) != cudaSuccess) return e;
   k_dz1<<<592, 256, 0, s>>>(m->dH1, m->Z1, B, Bp, w, m->dZ1h, m->dZ1Th, m->dZ1f);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (want_params) {
     k_colsum<<<w, 256, 0, s>>>(m->dZ1f, nullptr, B, w, m->gb1);
-    tcg::Operands o1{m->dZ1Th, m->xTh, w, d, Bp, Bp, Bp, nullptr};  // dW1 = dZ1^T x
+    tcg::Operands o1{m->dZ1Th, m->xTh, w, d, Bp, Bp, Bp, m->err};  // dW1 = dZ1^T x
     tcg::EpiStore e1{m->gW1, d, d};
     if ((e = tcg::launch(o1, e1, s)) != cudaSuccess) return e;
     if (t) k_mean<<<1, 256, 0, s>>>(m->sq, B, m->loss);
   }
   if (gx) {
-    tcg::Operands ox{m->dZ1h, m->W1Th, B, d, w, w, w, nullptr};  // dx = dZ1 W1
+    tcg::Operands ox{m->dZ1h, m->W1Th, B, d, w, w, w, m->err};  // dx = dZ1 W1
     tcg::EpiStore ex{gx, d, d};
     if ((e = tcg::launch(ox, ex, s)) != cudaSuccess) return e;
   }
@@ -359,6 +360,11 @@ tnmps_status tnmps_mlp_init(tnmps_mlp **out, int d_in, int width, int max_batch,
   m->dZ2f = (float *)p[i++];
   m->dZ1f = (float *)p[i++];
   m->loss = (float *)p[i++];
+  m->err = (uint32_t *)p[i++];
+  if (cudaMemset(m->err, 0, 4) != cudaSuccess) {
+    delete m;
+    return TNMPS_ERR_CUDA;
+  }
   const int d = d_in, w = width;
   auto views = [&](float *base, float **W1, float **b1, float **W2, float **b2, float **w3,
                    float **b3) {
@@ -386,6 +392,20 @@ void tnmps_mlp_free(tnmps_mlp *m) { delete m; }
 tnmps_status tnmps_mlp_set_stream(tnmps_mlp *m, void *stream) {
   if (!m) return TNMPS_ERR_ARG;
   m->stream = (cudaStream_t)stream;
+  return TNMPS_OK;
+}
+
+tnmps_status tnmps_mlp_check(tnmps_mlp *m) {
+  if (!m) return TNMPS_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  uint32_t flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flags, m->err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return mfail(m, e, "check");
+  if (flags & TNMPS_EFLAG_TIMEOUT) {
+    cudaMemset(m->err, 0, 4);
+    m->last_error = "a tensor-core GEMM wait ran out; results since the last check are invalid";
+    return TNMPS_ERR_TIMEOUT;
+  }
   return TNMPS_OK;
 }
 

@@ -125,6 +125,7 @@ struct tnmps_ctx {
   int n = 0, chi = 0, batch = 0, max_params = 0;
   tnmps_dtype dtype = TNMPS_C128;
   double eps = 1e-4;
+  float jacobi_tolfac = 1.0f;     // factor on the Jacobi orthogonality tolerance
   cudaStream_t stream = nullptr;
   char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -293,6 +294,9 @@ cudaError_t expect_run(tnmps_ctx *c, const TermPlan &p, char *ws, size_t ws_byte
                        double **per_term_used);
 // Workspace bytes of an expectation call; the per-term / energy result regions
 // are counted only when requested (the caller then supplies no device output).
+// failure-detection test kernel (k_diag.cu): a bounded wait that runs out
+cudaError_t launch_debug_wait(uint32_t *err, int64_t max_cycles, cudaStream_t s);
+
 size_t expect_ws_bytes(const tnmps_ctx *c, const TermPlan &p, int chunk, bool pt_region = true,
                        bool e_region = true);
 tnmps_status expect_noalloc_impl(tnmps_ctx *c, const TermPlan &p, uint64_t gen,

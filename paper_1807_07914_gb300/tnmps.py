@@ -18,7 +18,7 @@ OPS = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "RX": 8
        "RZ": 10, "CNOT": 16, "CZ": 17, "SWAP": 18}
 DTYPES = {"c128": 0, "c64": 1, "c64_bf16split": 2}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOMEM", 3: "ERR_UNSUPPORTED", 4: "ERR_NOT_CONVERGED",
-          5: "ERR_NUMERIC", 6: "ERR_CUDA", 7: "ERR_INJECTED"}
+          5: "ERR_NUMERIC", 6: "ERR_CUDA", 7: "ERR_INJECTED", 8: "ERR_TIMEOUT"}
 
 
 class TnmpsError(RuntimeError):
@@ -129,6 +129,9 @@ def lib():
         "tnmps_profile_read": (I, [P, P, P]),
         "tnmps_alu_peak_dev": (I, [I, I, I, P, C.POINTER(C.c_double), P]),
         "tnmps_set_tuning": (I, [P, C.POINTER(Tuning)]),
+        "tnmps_debug_wait_timeout": (I, [P, C.c_int64]),
+        "tnmps_set_svd_tolerance": (I, [P, D]),
+        "tnmps_mlp_check": (I, [P]),
         "tnmps_get_tuning": (I, [P, C.POINTER(Tuning)]),
     }
     for name, (res, args) in sig.items():
@@ -284,6 +287,10 @@ class MPSBatch:
 
     def set_cutoff(self, eps):
         self._check(lib().tnmps_set_cutoff(self._h, float(eps)))
+
+    def set_svd_tolerance(self, factor):
+        """Factor on the Jacobi SVD's orthogonality tolerance (1 = rounding level)."""
+        self._check(lib().tnmps_set_svd_tolerance(self._h, float(factor)))
 
     def reset(self):
         self._check(lib().tnmps_reset(self._h))
@@ -467,6 +474,11 @@ class MPSBatch:
         return {"jacobi_shape": [int(v) for v in t.jacobi_shape], "gemm_stages": int(t.gemm_stages),
                 "sweep_fused": int(t.sweep_fused)}
 
+    def debug_wait_timeout(self, max_cycles=2000000):
+        """Enqueue a device wait that runs out after max_cycles SM clocks and
+        raises the timeout flag (failure-detection tests)."""
+        self._check(lib().tnmps_debug_wait_timeout(self._h, int(max_cycles)))
+
     def inject(self, nth, status):
         self._check(lib().tnmps_debug_inject(self._h, int(nth), int(status)))
 
@@ -496,6 +508,10 @@ class Surrogate:
     def _check(self, st):
         if st != 0:
             raise TnmpsError(st, lib().tnmps_mlp_last_error(self._h).decode())
+
+    def check(self):
+        """Synchronise; raise if a tensor-core GEMM wait ran out since the last check."""
+        self._check(lib().tnmps_mlp_check(self._h))
 
     def set_params(self, p):
         p = torch.as_tensor(p, dtype=torch.float32, device=self.device).contiguous()

@@ -160,6 +160,7 @@ class Surrogate:
             for s in range(0, X.shape[0] - batch + 1, batch):
                 sel = perm[s:s + batch]
                 loss = self.net.train_step(Xd[sel], Yd[sel], lr)
+        self.net.check()
         return float(loss.item()) * self.sd ** 2 if loss is not None else None
 
     def predict(self, X):

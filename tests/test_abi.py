@@ -46,6 +46,7 @@ def test_host_only_entry_points(libt):
     L = libt.lib()
     assert L.tnmps_version().decode().startswith("tnmps")
     assert L.tnmps_status_string(4).decode() == "SVD did not converge"
+    assert L.tnmps_status_string(8).decode() == "device wait timed out"
     # arena size: grows with batch, rejects bad sizes
     a = L.tnmps_state_bytes(40, 128, 0, 1, 800)
     b = L.tnmps_state_bytes(40, 128, 0, 2, 800)
