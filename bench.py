@@ -359,9 +359,10 @@ def measure_alu_peaks(device):
     return out
 
 
-def jacobi_roofline(st, prof_jac, steps, t_local, peak, peak_src):
+def jacobi_roofline(st, prof_jac, steps, t_local, peak, peak_src, prof_lq=None):
     """The Jacobi SVD's roofline object: algorithmic flops per launch (device
-    counters) over its average event-timed launch duration."""
+    counters) over its average event-timed launch duration; with prof_lq, the
+    event-timed share of the LQ factorisation that precedes each Jacobi."""
     jac_ms, jac_n = prof_jac
     alg_flops = 8 * st["jacobi_pair_rows"] + 18 * st["jacobi_rot_rows"]
     exe_flops = 16 * st["jacobi_pair_rows"] + 18 * st["jacobi_rot_rows"]
@@ -376,7 +377,12 @@ def jacobi_roofline(st, prof_jac, steps, t_local, peak, peak_src):
             "executed_tflops": exe_flops / max(launches_per_step, 1) / avg_launch_s / 1e12,
             "alg_flops_per_launch": per_launch_alg, "avg_launch_ms": 1000 * avg_launch_s,
             "share_of_step": jac_ms / steps / (1000 * t_local / steps),
-            "sweeps_per_svd": st["jacobi_sweeps"] / max(st["svds"], 1)}
+            "sweeps_per_svd": st["jacobi_sweeps"] / max(st["svds"], 1),
+            "preconditioner": None if not prof_lq or not prof_lq[1] else {
+                "kernel": "k_lq_theta (Theta = L Q^H, Householder QR of Theta^H; the Jacobi "
+                          "runs on L)",
+                "ms_per_step": prof_lq[0] / steps, "launches_per_step": prof_lq[1] / steps,
+                "share_of_step": prof_lq[0] / steps / (1000 * t_local / steps)}}
 
 
 def accuracy(e_gpu, e_oracle, terms):
@@ -410,7 +416,7 @@ def fp64_form(args, wl, th_row0, e_oracle, alu, device):
     torch.cuda.synchronize(device)
     gates_c = tnmps.gate_array(wl["circuit"])
     m.reset()
-    m.profile(("jacobi",))
+    m.profile(("jacobi", "svd_lq"))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -424,7 +430,8 @@ def fp64_form(args, wl, th_row0, e_oracle, alu, device):
     st = m.stats()
     t = e0.elapsed_time(e1) / 1000.0
     roof = jacobi_roofline(st, prof["jacobi"], 1, t, alu["fp64_tflops"],
-                           "measured FP64 FMA rate (tnmps_alu_peak_dev, this run)")
+                           "measured FP64 FMA rate (tnmps_alu_peak_dev, this run)",
+                           prof["svd_lq"])
     return {"dtype": "c128", "batch": B, "steps": 1, "ms_per_step": 1000 * t,
             "value": B * T / t, "unit": UNIT, "gates_per_s": B * 390 / t,
             "gates_chi128_per_s": st["gates2q_full"] / t, "roofline": roof,
@@ -456,6 +463,7 @@ def run_gpu(args):
     m = tnmps.MPSBatch(n, chi, B, dtype=args.dtype, max_params=P, eps=eps, device=device)
     if args.dtype != "c128":
         m.set_svd_tolerance(args.svd_tolerance)
+    m.set_svd_precondition(args.svd_precondition)
     ps = tnmps.PauliSum(n, terms)
     gates_c = tnmps.gate_array(wl["circuit"])
     th_dev = torch.tensor(th, dtype=torch.float64, device=device)
@@ -514,7 +522,7 @@ def run_gpu(args):
     torch.cuda.synchronize(device)
     clocks.start()
     time.sleep(0.3)
-    m.profile(tnmps.PROF_CLASSES if args.profile_all else ("jacobi",))
+    m.profile(tnmps.PROF_CLASSES if args.profile_all else ("jacobi", "svd_lq"))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -545,9 +553,11 @@ def run_gpu(args):
         peak, peak_src = alu["fp32_tflops"], "measured FP32 FMA rate (tnmps_alu_peak_dev, this run)"
     else:
         peak, peak_src = alu["fp64_tflops"], "measured FP64 FMA rate (tnmps_alu_peak_dev, this run)"
-    roof = jacobi_roofline(st1, prof["jacobi"], args.steps, t_local, peak, peak_src)
+    roof = jacobi_roofline(st1, prof["jacobi"], args.steps, t_local, peak, peak_src,
+                           prof["svd_lq"])
     tr = profiled_traffic("k_jacobi_bench_step_304states_dram.md")
-    if tr is not None and args.dtype == "c64_bf16split" and B == 304:
+    if (tr is not None and args.dtype == "c64_bf16split" and B == 304
+            and args.svd_precondition == 1):
         roof["traffic"] = tr["bytes"]
         roof["traffic_over_alg_bytes"] = tr["bytes"] / roof["alg_bytes_per_launch"]
         roof["traffic_source"] = (tr["source"] + ": ncu dram__bytes_read.sum + "
@@ -580,7 +590,7 @@ def run_gpu(args):
             "dtype": args.dtype, "data": "synthetic",
             "config": dict(config_dict(args, n, chi, B, P, T, m.arena.numel()),
                            svd_tolerance_factor=args.svd_tolerance if args.dtype != "c128"
-                           else 1.0),
+                           else 1.0, svd_precondition=args.svd_precondition),
             "gates_per_s": gates_per_s,
             "gates_chi128_per_s": reduce_sum(full_per_step, ws, device) * args.steps / t,
             "phases_ms": {"circuit": circ_ms, "expect": exp_ms},
@@ -630,6 +640,8 @@ def main():
                     help="skip the pass over the 2000 random strings")
     ap.add_argument("--random-chunk", type=int, default=32,
                     help="states per expectation chunk of the random-string pass (untuned default)")
+    ap.add_argument("--svd-precondition", type=int, default=1, choices=(0, 1),
+                    help="1: the Jacobi SVD runs on L of Theta = L Q^H (default); 0: on Theta")
     ap.add_argument("--svd-tolerance", type=float, default=64.0,
                     help="factor on the Jacobi orthogonality tolerance of the complex64 forms "
                          "(1 = rounding level; 64 keeps the energies at the same accuracy "

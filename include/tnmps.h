@@ -131,7 +131,9 @@ typedef enum {
                              form; nested inside TNMPS_PROF_ENV)                */
   TNMPS_PROF_FIT = 8,     /* super-gate fit contractions: environments and the
                              two-site gradient (its splits count as JACOBI/SPLIT) */
-  TNMPS_PROF_NUM = 9
+  TNMPS_PROF_SVD_LQ = 9,  /* LQ factorisation of the two-site block ahead of the
+                             Jacobi SVD (tnmps_set_svd_precondition mode 1)   */
+  TNMPS_PROF_NUM = 10
 } tnmps_prof_class;
 
 const char *tnmps_status_string(tnmps_status s);
@@ -167,6 +169,17 @@ tnmps_status tnmps_set_cutoff(tnmps_ctx *ctx, double eps);
  * singular subspace correspondingly less exact. 1 <= factor <= 4096,
  * TNMPS_ERR_ARG otherwise. */
 tnmps_status tnmps_set_svd_tolerance(tnmps_ctx *ctx, double factor);
+/* What the Jacobi SVD of a two-site block (Sec. IV) orthogonalises.
+ *   mode 1 (default): the block Theta (M x N) is first factored as
+ *     Theta = L Q^H (Householder QR of Theta^H, Q not formed) and the Jacobi
+ *     runs on the columns of the lower-trapezoidal L (M x min(M, N)). Theta
+ *     and L have the same singular values and left singular vectors, and the
+ *     split forms U_k^H Theta from Theta itself, so the result is the same SVD;
+ *     L's columns start closer to orthogonal (their Gram matrix is one
+ *     QR-iteration step past Theta Theta^H), so fewer sweeps are needed.
+ *   mode 0: the Jacobi runs on the columns of Theta.
+ * TNMPS_ERR_ARG on any other mode. */
+tnmps_status tnmps_set_svd_precondition(tnmps_ctx *ctx, int mode);
 /* CUDA stream (cudaStream_t) for all work of this context; NULL = default. */
 tnmps_status tnmps_set_stream(tnmps_ctx *ctx, void *stream);
 /* Back to |0...0> with zero discarded weight and zeroed counters. */

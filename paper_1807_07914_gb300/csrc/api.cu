@@ -50,7 +50,7 @@ std::vector<int> bond_caps(int n, int chi) {
 }
 
 struct Layout {
-  size_t sites, site_off, dims, theta_buf, w_buf, sigma, perm, scale, discarded, theta_dev, err,
+  size_t sites, site_off, dims, theta_buf, w_buf, q_buf, sigma, perm, scale, discarded, theta_dev, err,
       counters, ebuf, tc_a, tc_b, total;
   int64_t tc_a_stride = 0, tc_b_stride = 0;  // per-state bytes of the K2 tensor-core operands
   int64_t state_elems, tw;
@@ -81,6 +81,8 @@ Layout make_layout(int n, int chi, int dtype, int batch, int max_params) {
   L.theta_buf = p;
   p = al256(p + esz * (size_t)batch * (size_t)L.tw);
   L.w_buf = p;
+  p = al256(p + esz * (size_t)batch * (size_t)L.tw);
+  L.q_buf = p;
   p = al256(p + esz * (size_t)batch * (size_t)L.tw);
   L.sigma = p;
   p = al256(p + 8 * (size_t)batch * 2 * chi);
@@ -635,6 +637,7 @@ tnmps_status tnmps_init(tnmps_ctx **out, int n, int chi, tnmps_dtype dtype, int 
   c->dims = (int32_t *)(c->arena + L.dims);
   c->theta_buf = c->arena + L.theta_buf;
   c->w_buf = c->arena + L.w_buf;
+  c->q_buf = c->arena + L.q_buf;
   c->sigma = (double *)(c->arena + L.sigma);
   c->perm = (int32_t *)(c->arena + L.perm);
   c->scale = (double *)(c->arena + L.scale);
@@ -1329,6 +1332,13 @@ tnmps_status tnmps_set_svd_tolerance(tnmps_ctx *c, double factor) {
   if (!(factor >= 1.0 && factor <= 4096.0))
     return fail(c, TNMPS_ERR_ARG, "tolerance factor must lie in [1, 4096]");
   c->jacobi_tolfac = (float)factor;
+  return TNMPS_OK;
+}
+
+tnmps_status tnmps_set_svd_precondition(tnmps_ctx *c, int mode) {
+  if (!c) return TNMPS_ERR_ARG;
+  if (mode != 0 && mode != 1) return fail(c, TNMPS_ERR_ARG, "svd precondition mode must be 0 or 1");
+  c->svd_lq = mode;
   return TNMPS_OK;
 }
 

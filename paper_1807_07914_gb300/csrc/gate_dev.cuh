@@ -526,4 +526,37 @@ __device__ int lq_left_cta(cx<R> *X, int Dl, int Dr, cx<R> *W, cx<R> *Qbuf) {
   return r;
 }
 
+// LQ of a two-site block ahead of its SVD: T (M x N row-major) = L Q^H via
+// the QR of T^H = Q R'. Q is not formed: T and L have the same singular values
+// and left singular vectors, which is all the split uses (it forms U_k^H T
+// from T). Wq (N x M column-major scratch) receives T^H and is factored in
+// place; L = R'^H goes column-major (ld M) to Lout: lower trapezoidal, r =
+// min(M, N) columns, and columns r..N-1 zero. Returns r. Whole CTA. HR as in
+// qr_right_cta (N <= 32 HR).
+template <typename R, int HR = 0, int NB = sizeof(R) == 4 ? 8 : 4>
+__device__ int lq_theta_cta(const cx<R> *T, int M, int N, cx<R> *Wq, cx<R> *Lout) {
+  const int m = N, n = M, r = m < n ? m : n;
+  __shared__ cx<R> tau[2 * TNMPS_MAX_CHI];
+  __shared__ cx<R> vs[2 * TNMPS_MAX_CHI];
+  __shared__ R red[32];
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * n; e += blockDim.x) Wq[e] = cconj(T[e]);
+  __syncthreads();
+  if constexpr (HR > 0 &&
+                (NB * 32 * HR + 4 * TNMPS_MAX_CHI) * sizeof(cx<R>) <= 40960) {
+    __shared__ cx<R> Ts[NB * NB], Gs[NB * NB];
+    __shared__ __align__(16) cx<R> Vs[NB * 32 * HR];  // the panel's reflectors
+    householder_qr_blocked<R, NB, HR>(Wq, m, n, tau, red, vs, Ts, Gs, Vs);
+  } else {
+    householder_qr(Wq, m, n, tau, red, vs);
+  }
+  // L[p][q] = conj(R'[q][p]) for p >= q, q < r; R'[q][p] sits at Wq[q + p m]
+  for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
+    const int q = e / M, p = e - q * M;
+    Lout[e] = (q < r && p >= q) ? cconj(Wq[(int64_t)p * m + q]) : mkc<R>(0, 0);
+  }
+  __syncthreads();
+  return r;
+}
+
 }  // namespace gdev

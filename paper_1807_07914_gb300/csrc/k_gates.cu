@@ -21,7 +21,7 @@
 #include "gemm_tile.cuh"
 #include "tnmps_internal.h"
 
-cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap);
+cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap, bool lq);
 
 namespace {
 
@@ -319,6 +319,16 @@ __global__ void __launch_bounds__(256) k_lq_left(StateView v, int c, cx<R> *wbuf
   if (threadIdx.x == 0) newdim[b] = r;
 }
 
+// K3 preconditioner: Theta (theta_buf, row-major 2D_{l-1} x 2D_{l+1}) = L Q^H;
+// L (column-major, the Jacobi input) -> w_buf, Householder scratch in qbuf.
+template <typename R, int HR>
+__global__ void __launch_bounds__(256) k_lq_theta(StateView v, int l, const cx<R> *tbuf,
+                                                  cx<R> *qbuf, cx<R> *wbuf, int64_t tw) {
+  const int b = blockIdx.x;
+  gdev::lq_theta_cta<R, HR>(tbuf + (int64_t)b * tw, 2 * dimv(v, b, l), 2 * dimv(v, b, l + 2),
+                            qbuf + (int64_t)b * tw, wbuf + (int64_t)b * tw);
+}
+
 // out (r x 2D') = R (r x Dr, upper triangle of w_buf, ld 2Dl) * B_{c+1} (Dr x 2D')
 template <typename R>
 struct ProbRB {
@@ -453,9 +463,20 @@ cudaError_t split_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   prof_end(c, PC_THETA, ev);
-  // K3: one-sided Jacobi on the column-major copy
+  if (c->svd_lq) {  // Theta = L Q^H: the Jacobi input becomes L (same sigma and U)
+    ev = prof_begin(c, PC_SVD_LQ);
+    cx<R> *qb = reinterpret_cast<cx<R> *>(c->q_buf);
+    if (Nmax <= 256)
+      k_lq_theta<R, 8><<<c->batch, 256, 0, c->stream>>>(v, l, tb, qb, wb, c->tw);
+    else
+      k_lq_theta<R, 16><<<c->batch, 256, 0, c->stream>>>(v, l, tb, qb, wb, c->tw);
+    ++c->launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    prof_end(c, PC_SVD_LQ, ev);
+  }
+  // K3: one-sided Jacobi on the column-major copy (or on L)
   ev = prof_begin(c, PC_JACOBI);
-  if ((e = launch_jacobi_gate(c, l, Mmax)) != cudaSuccess) return e;
+  if ((e = launch_jacobi_gate(c, l, Mmax, c->svd_lq != 0)) != cudaSuccess) return e;
   ++c->launches;
   prof_end(c, PC_JACOBI, ev);
   // K4: rank, A_l <- U_k, [orthonormalise U_k], C_{l+1} <- U_k^H Theta, normalise

@@ -30,6 +30,7 @@ struct JacobiArgs {
   int64_t stride;          // elements between matrices
   const int32_t *dims;     // gate mode: M = 2 dims[b][l], N = 2 dims[b][l+2]
   int dstride, l;
+  int n_le_m;              // gate mode: N capped at M (the input is L of Theta = L Q^H)
   int m, n, lda;           // fixed mode (dims == nullptr)
   double *sigma_out;       // optional [batch][n]
   int32_t *sweeps_out;     // optional [batch]
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(NT, MINB) k_jacobi(JacobiArgs p) {
   if (p.dims) {
     M = 2 * p.dims[(int64_t)b * p.dstride + p.l];
     N = 2 * p.dims[(int64_t)b * p.dstride + p.l + 2];
+    if (p.n_le_m && N > M) N = M;  // L has M columns; the rest of the buffer is zero
     ld = M;
   } else {
     M = p.m;
@@ -131,13 +133,15 @@ cudaError_t dispatch(const JacobiArgs &a, int Mcap, int batch, cudaStream_t s,
 }  // namespace
 
 // gate mode: matrix of state b is the W buffer, M = 2 D_{l-1}, N = 2 D_{l+1}
-cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap) {
+// (lq: W holds L of Theta = L Q^H, min(M, N) columns)
+cudaError_t launch_jacobi_gate(tnmps_ctx *c, int l, int Mcap, bool lq) {
   JacobiArgs a{};
   a.W = c->w_buf;
   a.stride = c->tw;
   a.dims = c->dims;
   a.dstride = c->n + 1;
   a.l = l;
+  a.n_le_m = lq ? 1 : 0;
   a.max_sweeps = c->dtype == TNMPS_C128 ? 40 : 30;
   a.tolfac = c->jacobi_tolfac;
   a.err = c->err;

@@ -70,7 +70,8 @@ enum {
 
 // kernel classes for event timing (mirrors tnmps_prof_class in tnmps.h)
 enum {
-  PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_ENV_TC, PC_FIT, PC_NUM
+  PC_THETA = 0, PC_JACOBI, PC_SPLIT, PC_MOVE, PC_GATE1, PC_ENV, PC_TERM, PC_ENV_TC, PC_FIT,
+  PC_SVD_LQ, PC_NUM
 };
 
 // ---------------------------------------------------------------- ops
@@ -126,6 +127,7 @@ struct tnmps_ctx {
   tnmps_dtype dtype = TNMPS_C128;
   double eps = 1e-4;
   float jacobi_tolfac = 1.0f;     // factor on the Jacobi orthogonality tolerance
+  int svd_lq = 1;                 // 1: Jacobi on L of Theta = L Q^H (0: on Theta)
   cudaStream_t stream = nullptr;
   char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -136,6 +138,7 @@ struct tnmps_ctx {
   int32_t *dims = nullptr;
   void *theta_buf = nullptr;   // [batch][tw] row-major Theta (gate applied)
   void *w_buf = nullptr;       // [batch][tw] column-major Jacobi working copy
+  void *q_buf = nullptr;       // [batch][tw] Householder scratch of the block's LQ
   double *sigma = nullptr;     // [batch][2chi]
   int32_t *perm = nullptr;     // [batch][2chi]
   double *scale = nullptr;     // [batch]

@@ -51,7 +51,8 @@ class Stats(C.Structure):
                                           "launches", "jacobi_alg_bytes")]
 
 
-PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term", "env_tc", "fit")
+PROF_CLASSES = ("theta", "jacobi", "split", "move", "gate1", "env", "term", "env_tc", "fit",
+                "svd_lq")
 
 
 _lib = None
@@ -131,6 +132,7 @@ def lib():
         "tnmps_set_tuning": (I, [P, C.POINTER(Tuning)]),
         "tnmps_debug_wait_timeout": (I, [P, C.c_int64]),
         "tnmps_set_svd_tolerance": (I, [P, D]),
+        "tnmps_set_svd_precondition": (I, [P, I]),
         "tnmps_mlp_check": (I, [P]),
         "tnmps_get_tuning": (I, [P, C.POINTER(Tuning)]),
     }
@@ -291,6 +293,11 @@ class MPSBatch:
     def set_svd_tolerance(self, factor):
         """Factor on the Jacobi SVD's orthogonality tolerance (1 = rounding level)."""
         self._check(lib().tnmps_set_svd_tolerance(self._h, float(factor)))
+
+    def set_svd_precondition(self, mode):
+        """1 (default): the Jacobi SVD runs on L of Theta = L Q^H (same singular
+        values and left vectors, fewer sweeps); 0: on Theta itself."""
+        self._check(lib().tnmps_set_svd_precondition(self._h, int(mode)))
 
     def reset(self):
         self._check(lib().tnmps_reset(self._h))

@@ -21,6 +21,10 @@ Bars:
   error per step), provided the chi_max cut has a gap of at least 1e-5 sigma_0
   at every step (the FP32 SVD's resolution); also with the Jacobi tolerance
   factor 64 that the benchmark uses.
+
+Every case runs with the Jacobi on L of Theta = L Q^H (the default) and the
+complex128 and complex64 forms also with the Jacobi on Theta itself; both
+must meet the same bars, and the LQ form needs fewer sweeps.
 """
 import numpy as np
 import pytest
@@ -62,15 +66,23 @@ def reference():
     return wl, rand, rows
 
 
-@pytest.mark.parametrize("dtype,svd_tol", [("c128", 1), ("c64", 1), ("c64_bf16split", 1),
-                                           ("c64_bf16split", 64)])
-def test_chi128_workload_against_oracle(reference, dtype, svd_tol):
-    """svd_tol 64: the Jacobi tolerance factor the benchmark runs with."""
+SWEEPS = {}
+
+
+@pytest.mark.parametrize("dtype,svd_tol,lq", [("c128", 1, 1), ("c64", 1, 1),
+                                              ("c64_bf16split", 1, 1), ("c64_bf16split", 64, 1),
+                                              ("c128", 1, 0), ("c64", 1, 0)])
+def test_chi128_workload_against_oracle(reference, dtype, svd_tol, lq):
+    """svd_tol 64: the Jacobi tolerance factor the benchmark runs with; lq:
+    the Jacobi on L of Theta = L Q^H (1) or on Theta (0)."""
     wl, rand, rows = reference
     m = tnmps.MPSBatch(wl["n"], wl["chi_max"], ROWS, dtype=dtype, max_params=wl["n_params"],
                        eps=wl["eps"])
     m.set_svd_tolerance(svd_tol)
+    m.set_svd_precondition(lq)
     m.apply_circuit(wl["circuit"], wl["thetas"][:ROWS])
+    st = m.stats()
+    SWEEPS[(dtype, svd_tol, lq)] = st["jacobi_sweeps"] / st["svds"]
     eh, pth = m.expect(tnmps.PauliSum(wl["n"], wl["terms"]), per_term=True)
     er, ptr = m.expect(tnmps.PauliSum(wl["n"], rand), per_term=True)
     m.check()
@@ -97,3 +109,14 @@ def test_chi128_workload_against_oracle(reference, dtype, svd_tol):
             assert abs(w[b] - r["w"]) <= 1e-4 * r["w"], msg
         assert abs(eh[b] - eh_ref) <= 1e-6 * sh, msg
         assert abs(er[b] - er_ref) <= 1e-6 * sr, msg
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_lq_form_needs_fewer_sweeps(dtype):
+    """Theta = L Q^H: the columns of L start closer to orthogonal (their Gram
+    matrix is one QR-iteration step past Theta Theta^H), so the Jacobi on L
+    converges in fewer sweeps than on Theta (both pass the oracle bars above)."""
+    on, off = SWEEPS.get((dtype, 1, 1)), SWEEPS.get((dtype, 1, 0))
+    if on is None or off is None:
+        pytest.skip("runs after the parity cases of this module")
+    assert on < off, (dtype, on, off)

@@ -73,6 +73,10 @@ def test_bad_tuning_rejected():
         with pytest.raises(tnmps.TnmpsError) as ei:
             m.set_svd_tolerance(bad)
         assert ei.value.status == 1
+    for bad in (-1, 2):
+        with pytest.raises(tnmps.TnmpsError) as ei:
+            m.set_svd_precondition(bad)
+        assert ei.value.status == 1
 
 
 @pytest.mark.parametrize("chunk", [0, 3])
