@@ -53,7 +53,7 @@ struct BatchArgs {
   uint32_t *err;
   char *scratch;
   int64_t stride;  // scratch bytes per CTA
-  int64_t o_state, o_t, o_w, o_e, o_renv, o_env, o_tm;
+  int64_t o_state, o_t, o_w, o_e, o_renv, o_env, o_tm, o_q;
   int chi_cap;
   double eps_eff;
 };
@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
   cx<R> *renv = reinterpret_cast<cx<R> *>(base + a.o_renv);
   cx<R> *envs = reinterpret_cast<cx<R> *>(base + a.o_env);
   cx<R> *Tm = reinterpret_cast<cx<R> *>(base + a.o_tm);
+  cx<R> *Qs = reinterpret_cast<cx<R> *>(base + a.o_q);  // Householder scratch of the LQ
   const int64_t env_elems = (int64_t)a.chi_cap * a.chi_cap;
   const int tid = threadIdx.x;
 
@@ -228,10 +229,13 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
         __syncthreads();
         gdev::apply_gate4_range<R>(G, T, W, Dl, Dr, tid, blockDim.x);
         __syncthreads();
+        // Theta = L Q^H: the Jacobi runs on L (same singular values and left
+        // vectors, fewer sweeps); its columns past min(M, N) are zero
+        const int r = gdev::lq_theta_cta<R, 8>(T, M, N, Qs, W);
         bool conv;
         int rot, chk;
         // 8 warps: with 16-column blocks each warp keeps its two x columns in registers
-        jac::jacobi_run<R, BC, 8, BC == 16, BC == 16>(W, M, N, M, S0, S1, 1.0f, 30, &conv, &rot,
+        jac::jacobi_run<R, BC, 8, BC == 16, BC == 16>(W, M, r, M, S0, S1, 1.0f, 30, &conv, &rot,
                                                       &chk, S2);
         if (!conv && N > 1) {
           if (tid == 0) atomicOr(a.err, TNMPS_EFLAG_NOT_CONVERGED);
@@ -402,7 +406,7 @@ int64_t state_elems(int n, int chi) {
 }
 
 struct Sizes {
-  int64_t o_state, o_t, o_w, o_e, o_renv, o_env, o_tm, stride;
+  int64_t o_state, o_t, o_w, o_e, o_renv, o_env, o_tm, o_q, stride;
   size_t plan_bytes, total;
   size_t o_jobs, o_order, o_ops, o_facs, o_cores, o_thetas, o_nodes, o_energy, o_disc, o_counter,
       o_err, o_scratch;
@@ -424,6 +428,7 @@ Sizes sizes(const tnmps_batch *b, int grid) {
   s.o_renv = put(8 * b->renv_max);
   s.o_env = put(8 * c2 * std::max(b->depth_max, 1));
   s.o_tm = put(8 * 2 * c2);
+  s.o_q = put(8 * 4 * c2);
   s.stride = o;
   size_t p = 0;
   auto plan = [&](size_t bytes) {
@@ -693,6 +698,7 @@ tnmps_status tnmps_batch_bind(tnmps_batch *b, void *arena, size_t bytes, int cta
   a.o_renv = s.o_renv;
   a.o_env = s.o_env;
   a.o_tm = s.o_tm;
+  a.o_q = s.o_q;
   a.chi_cap = b->chi_cap;
   const double floor = 8.0 * 5.9604644775390625e-08;
   a.eps_eff = b->cutoff > floor ? b->cutoff : floor;
