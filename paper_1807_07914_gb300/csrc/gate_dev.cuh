@@ -134,13 +134,13 @@ __device__ __forceinline__ R block_sum(R v, R *red) {
 // the trailing block, w = v^H x (warp reduction) and x -= coef * w * v. The
 // reflector v sits in shared memory (vs, entries j..m-1, vs[j] = 1) and a
 // warp keeps its column in registers between the dot and the update
-// (m <= 32 * HR).
+// (m <= 32 * HR). Row i of column k sits at X[k * ldx + i - roff].
 template <typename R, int HR>
 __device__ __forceinline__ void reflect_columns(cx<R> *X, int ldx, int k0, int k1, int j, int m,
-                                                const cx<R> *vs, cx<R> coef) {
+                                                const cx<R> *vs, cx<R> coef, int roff = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int k = k0 + warp; k < k1; k += nw) {
-    cx<R> *x = X + (int64_t)k * ldx;
+    cx<R> *x = X + (int64_t)k * ldx - roff;
     cx<R> xr[HR];
     cx<R> w = mkc<R>(0, 0);
 #pragma unroll
@@ -307,65 +307,81 @@ __device__ void block_tfactor(const cx<R> *Vs, int j0, int nb, int m, const cx<R
 
 // Columns k0..k1-1 of X (ld ldx): x <- (I - V op(T) V^H) x with op(T) = T^H
 // (herm: the QR trailing update, H^H of each reflector in order) or T (forming
-// Q). Only rows >= j0 change. Warp per column, the column in registers
-// (m - j0 <= 32 HR).
+// Q). Only rows >= j0 change. A warp takes two columns at a time, both in
+// registers (m - j0 <= 32 HR), so each staged reflector value read from
+// shared memory serves two columns.
 template <typename R, int HR, int NB>
 __device__ void apply_block_reflector(cx<R> *X, int ldx, int k0, int k1, const cx<R> *Vs,
                                       int j0, int m, const cx<R> *Ts, bool herm) {
   constexpr int VLD = 32 * HR;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int col = k0 + warp; col < k1; col += nw) {
-    cx<R> *x = X + (int64_t)col * ldx;
-    cx<R> xr[HR];
-    R w[2 * NB];
+  for (int col = k0 + 2 * warp; col < k1; col += 2 * nw) {
+    const bool two = col + 1 < k1;
+    cx<R> *x0 = X + (int64_t)col * ldx;
+    cx<R> *x1 = x0 + ldx;
+    cx<R> xr[2][HR];
+    R w[4 * NB];  // column 0: w[0 .. 2NB), column 1: w[2NB .. 4NB)
 #pragma unroll
-    for (int k = 0; k < 2 * NB; ++k) w[k] = R(0);
+    for (int k = 0; k < 4 * NB; ++k) w[k] = R(0);
 #pragma unroll
     for (int h = 0; h < HR; ++h) {
       const int i = j0 + lane + 32 * h;
-      xr[h] = i < m ? x[i] : mkc<R>(0, 0);
+      xr[0][h] = i < m ? x0[i] : mkc<R>(0, 0);
+      xr[1][h] = (two && i < m) ? x1[i] : mkc<R>(0, 0);
       if (i < m) {
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
           const cx<R> v = Vs[k * VLD + lane + 32 * h];
-          w[2 * k] = fma(v.re, xr[h].re, fma(v.im, xr[h].im, w[2 * k]));
-          w[2 * k + 1] = fma(v.re, xr[h].im, fma(-v.im, xr[h].re, w[2 * k + 1]));
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            R *wq = w + 2 * NB * q;
+            wq[2 * k] = fma(v.re, xr[q][h].re, fma(v.im, xr[q][h].im, wq[2 * k]));
+            wq[2 * k + 1] = fma(v.re, xr[q][h].im, fma(-v.im, xr[q][h].re, wq[2 * k + 1]));
+          }
         }
       }
     }
-    warp_allsum<R, 2 * NB>(w, lane);
+    warp_allsum<R, 4 * NB>(w, lane);
     // w <- op(T) w in place: T upper (rows ascending), T^H lower (rows descending)
-    if (herm) {
 #pragma unroll
-      for (int i = NB - 1; i >= 0; --i) {
-        cx<R> a = mkc<R>(0, 0);
+    for (int q = 0; q < 2; ++q) {
+      R *wq = w + 2 * NB * q;
+      if (herm) {
 #pragma unroll
-        for (int k = 0; k <= i; ++k) cfma(a, cconj(Ts[k * NB + i]), mkc<R>(w[2 * k], w[2 * k + 1]));
-        w[2 * i] = a.re;
-        w[2 * i + 1] = a.im;
-      }
-    } else {
+        for (int i = NB - 1; i >= 0; --i) {
+          cx<R> a = mkc<R>(0, 0);
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        cx<R> a = mkc<R>(0, 0);
+          for (int k = 0; k <= i; ++k)
+            cfma(a, cconj(Ts[k * NB + i]), mkc<R>(wq[2 * k], wq[2 * k + 1]));
+          wq[2 * i] = a.re;
+          wq[2 * i + 1] = a.im;
+        }
+      } else {
 #pragma unroll
-        for (int k = i; k < NB; ++k) cfma(a, Ts[i * NB + k], mkc<R>(w[2 * k], w[2 * k + 1]));
-        w[2 * i] = a.re;
-        w[2 * i + 1] = a.im;
+        for (int i = 0; i < NB; ++i) {
+          cx<R> a = mkc<R>(0, 0);
+#pragma unroll
+          for (int k = i; k < NB; ++k) cfma(a, Ts[i * NB + k], mkc<R>(wq[2 * k], wq[2 * k + 1]));
+          wq[2 * i] = a.re;
+          wq[2 * i + 1] = a.im;
+        }
       }
     }
 #pragma unroll
     for (int h = 0; h < HR; ++h) {
       const int i = j0 + lane + 32 * h;
       if (i < m) {
-        cx<R> a = xr[h];
+        cx<R> a0 = xr[0][h], a1 = xr[1][h];
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
           const cx<R> v = Vs[k * VLD + lane + 32 * h];
-          a.re -= v.re * w[2 * k] - v.im * w[2 * k + 1];
-          a.im -= v.re * w[2 * k + 1] + v.im * w[2 * k];
+          a0.re -= v.re * w[2 * k] - v.im * w[2 * k + 1];
+          a0.im -= v.re * w[2 * k + 1] + v.im * w[2 * k];
+          a1.re -= v.re * w[2 * NB + 2 * k] - v.im * w[2 * NB + 2 * k + 1];
+          a1.im -= v.re * w[2 * NB + 2 * k + 1] + v.im * w[2 * NB + 2 * k];
         }
-        x[i] = a;
+        x0[i] = a0;
+        if (two) x1[i] = a1;
       }
     }
   }
@@ -374,19 +390,29 @@ __device__ void apply_block_reflector(cx<R> *X, int ldx, int k0, int k1, const c
 // householder_qr with panels of NB reflectors: each panel is factored with
 // the reflector-at-a-time loop restricted to its own columns, then its block
 // reflector updates the trailing columns once. Same output as householder_qr.
+// The panel (rows j0..m-1 of its nb columns) is factored in shared memory, in
+// Vs (panel column k, row i at Vs[k * VLD + i - j0]), written back to W once,
+// and then turned in place into the staged reflectors of the trailing update.
 template <typename R, int NB, int HR>
 __device__ void householder_qr_blocked(cx<R> *W, int m, int n, cx<R> *tau, R *red, cx<R> *vs,
                                        cx<R> *Ts, cx<R> *Gs, cx<R> *Vs) {
+  constexpr int VLD = 32 * HR;
   const int r = m < n ? m : n;
   for (int j0 = 0; j0 < r; j0 += NB) {
     const int nb = r - j0 < NB ? r - j0 : NB;
+    const int rows = m - j0;
+    for (int e = threadIdx.x; e < nb * VLD; e += blockDim.x) {
+      const int k = e / VLD, ii = e - k * VLD;
+      if (ii < rows) Vs[e] = W[(int64_t)(j0 + k) * m + j0 + ii];
+    }
+    __syncthreads();
     for (int j = j0; j < j0 + nb; ++j) {
-      cx<R> *col = W + (int64_t)j * m;
+      cx<R> *col = Vs + (j - j0) * VLD;  // row i at col[i - j0]
       R part = 0;
       for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
-        part += col[i].re * col[i].re + col[i].im * col[i].im;
+        part += col[i - j0].re * col[i - j0].re + col[i - j0].im * col[i - j0].im;
       const R xn2 = block_sum(part, red);
-      const cx<R> alpha = col[j];
+      const cx<R> alpha = col[j - j0];
       __syncthreads();
       cx<R> tj = mkc<R>(0, 0);
       if (!(xn2 == R(0) && alpha.im == R(0))) {
@@ -396,25 +422,38 @@ __device__ void householder_qr_blocked(cx<R> *W, int m, int n, cx<R> *tau, R *re
         const R den = dr * dr + di * di;
         const cx<R> sc = mkc<R>(dr / den, -di / den);
         for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-          const cx<R> v = cmul(col[i], sc);
-          col[i] = v;
+          const cx<R> v = cmul(col[i - j0], sc);
+          col[i - j0] = v;
           vs[i] = v;
         }
         if (threadIdx.x == 0) {
-          col[j] = mkc<R>(beta, 0);
+          col[j - j0] = mkc<R>(beta, 0);
           vs[j] = mkc<R>(1, 0);
         }
       }
       if (threadIdx.x == 0) tau[j] = tj;
       __syncthreads();
       if ((tj.re == R(0) && tj.im == R(0)) || j + 1 >= j0 + nb) continue;
-      if (m <= 256) reflect_columns<R, 8>(W, m, j + 1, j0 + nb, j, m, vs, cconj(tj));
-      else reflect_columns<R, 16>(W, m, j + 1, j0 + nb, j, m, vs, cconj(tj));
+      // panel columns j+1..j0+nb-1 (column index relative to the panel)
+      reflect_columns<R, HR>(Vs, VLD, j + 1 - j0, nb, j, m, vs, cconj(tj), j0);
       __syncthreads();
     }
+    // R on and above the diagonal, the reflectors below it
+    for (int e = threadIdx.x; e < nb * VLD; e += blockDim.x) {
+      const int k = e / VLD, ii = e - k * VLD;
+      if (ii < rows) W[(int64_t)(j0 + k) * m + j0 + ii] = Vs[e];
+    }
+    __syncthreads();
     if (j0 + nb >= n) continue;
-    stage_panel<R, NB, 32 * HR>(W, m, j0, nb, m, Vs);
-    block_tfactor<R, NB, 32 * HR>(Vs, j0, nb, m, tau, Ts, Gs);
+    // staged reflectors (as stage_panel): explicit 1 on the diagonal, 0 above,
+    // rows >= m and columns >= nb zero
+    for (int e = threadIdx.x; e < NB * VLD; e += blockDim.x) {
+      const int k = e / VLD, ii = e - k * VLD;
+      const cx<R> z = mkc<R>(0, 0);
+      Vs[e] = (k < nb && ii < rows) ? (ii > k ? Vs[e] : (ii == k ? mkc<R>(1, 0) : z)) : z;
+    }
+    __syncthreads();
+    block_tfactor<R, NB, VLD>(Vs, j0, nb, m, tau, Ts, Gs);
     apply_block_reflector<R, HR, NB>(W, m, j0 + nb, n, Vs, j0, m, Ts, true);
     __syncthreads();
   }
