@@ -7,8 +7,8 @@
 namespace gdev {
 
 // Theta = G X on the physical pair for elements e = start, start+stride, ...
-// of the Dl x Dr grid; T row-major (2Dl) x (2Dr) in place, W its
-// column-major copy (the Jacobi input).
+// of the Dl x Dr grid; T row-major (2Dl) x (2Dr) in place, W (unless null)
+// its column-major copy (the Jacobi input on Theta itself).
 template <typename R>
 __device__ __forceinline__ void apply_gate4_range(const cx<R> *G, cx<R> *T, cx<R> *W, int Dl,
                                                   int Dr, int start, int stride) {
@@ -25,7 +25,7 @@ __device__ __forceinline__ void apply_gate4_range(const cx<R> *G, cx<R> *T, cx<R
       for (int q = 0; q < 4; ++q) cfma(acc, G[4 * r + q], x[q]);
       const int i = 2 * a + (r >> 1), j = (r & 1) * Dr + c;
       T[(int64_t)i * N + j] = acc;
-      W[(int64_t)j * M + i] = acc;
+      if (W) W[(int64_t)j * M + i] = acc;
     }
   }
 }
@@ -34,23 +34,27 @@ __device__ __forceinline__ void apply_gate4_range(const cx<R> *G, cx<R> *T, cx<R
 // values = column norms (FP64), stable descending order, keep those >=
 // e_eff * ||sigma|| (and > 0), at most min(cap, M, N), at least one;
 // A (M x k row-major) <- normalised kept columns. Returns k; *w = discarded
-// weight of the step; *bad = non-finite or zero norm. Whole CTA.
+// weight of the step; *bad = non-finite or zero norm. Whole CTA. A lane sums
+// its share of a column in R (FP32 for complex64: the columns carry FP32
+// rounding already), the warp reduction runs in FP64.
 template <typename R>
 __device__ int select_cta(const cx<R> *W, int M, int N, int cap, double e_eff, cx<R> *A, double *w,
                           bool *bad) {
   __shared__ double sig[TNMPS_JACOBI_MAX_DIM];
   __shared__ int perm[TNMPS_JACOBI_MAX_DIM];
+  __shared__ R inv_s[TNMPS_JACOBI_MAX_DIM];  // 1 / sigma of the kept column of rank r
   __shared__ int s_k;
   __shared__ double s_w;
   __shared__ bool s_bad;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   for (int j = warp; j < N; j += nw) {
-    double acc = 0;
+    R part = 0;
     for (int r = lane; r < M; r += 32) {
       const cx<R> z = W[(int64_t)j * M + r];
-      acc += (double)z.re * z.re + (double)z.im * z.im;
+      part = fma(z.re, z.re, fma(z.im, z.im, part));
     }
+    double acc = (double)part;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) sig[j] = sqrt(acc);
@@ -84,12 +88,15 @@ __device__ int select_cta(const cx<R> *W, int M, int N, int cap, double e_eff, c
   }
   __syncthreads();
   const int k = s_k;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    const double s = sig[perm[r]];
+    inv_s[r] = s > 0 ? (R)(1.0 / s) : R(0);
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < M * k; e += blockDim.x) {
     const int i = e / k, r = e - i * k;
-    const int j = perm[r];
-    const double s = sig[j];
-    const R inv = s > 0 ? (R)(1.0 / s) : R(0);
-    const cx<R> z = W[(int64_t)j * M + i];
+    const R inv = inv_s[r];
+    const cx<R> z = W[(int64_t)perm[r] * M + i];
     A[e] = mkc<R>(z.re * inv, z.im * inv);
   }
   *w = s_w;
@@ -98,13 +105,22 @@ __device__ int select_cta(const cx<R> *W, int M, int N, int cap, double e_eff, c
   return k;
 }
 
-// X (cnt elements) <- X / ||X||_F (FP64 sum). Whole CTA.
+// X (cnt elements) <- X / ||X||_F (FP64 sum of R partial sums over runs of 8
+// elements). Whole CTA.
 template <typename R>
 __device__ void normalise_cta(cx<R> *X, int cnt) {
   __shared__ double red[32];
   double acc = 0;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x)
-    acc += (double)X[e].re * X[e].re + (double)X[e].im * X[e].im;
+  // runs of 8 of a thread's elements summed in R, the runs in FP64
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += 8 * blockDim.x) {
+    R part = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < cnt) part = fma(X[e].re, X[e].re, fma(X[e].im, X[e].im, part));
+    }
+    acc += (double)part;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __syncthreads();

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256, 1) k_batch(BatchArgs a) {
           for (int e = 0; e < 16; ++e) G[e] = mkc<R>((R)Gd[e].re, (R)Gd[e].im);
         }
         __syncthreads();
-        gdev::apply_gate4_range<R>(G, T, W, Dl, Dr, tid, blockDim.x);
+        gdev::apply_gate4_range<R>(G, T, nullptr, Dl, Dr, tid, blockDim.x);
         __syncthreads();
         // Theta = L Q^H: the Jacobi runs on L (same singular values and left
         // vectors, fewer sweeps); its columns past min(M, N) are zero

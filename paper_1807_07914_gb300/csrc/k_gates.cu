@@ -78,8 +78,8 @@ struct ProbTheta {
   __device__ void store(int i, int j, cx<R> val) const { C[(int64_t)i * ldc + j] = val; }
 };
 
-// Theta = G X on the physical pair; writes theta_buf (in place) and the
-// column-major Jacobi copy in w_buf. A CTA takes a in [a0, a0+16) and c in
+// Theta = G X on the physical pair; writes theta_buf (in place) and, unless
+// wbuf is null, the column-major Jacobi copy in w_buf. A CTA takes a in [a0, a0+16) and c in
 // [c0, c0+32), i.e. Theta rows 2a0..2a0+31 and columns c0.. and Dr+c0.. of
 // both physical halves: the row-major result goes back along rows, and W is
 // written column by column from a shared-memory transpose of the tile.
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_apply_gate4(StateView v, Op2 op, const 
   if (a0 >= Dl || c0 >= Dr) return;  // uniform over the CTA
   const int M = 2 * Dl, N = 2 * Dr;
   cx<R> *T = tbuf + (int64_t)b * tw;
-  cx<R> *W = wbuf + (int64_t)b * tw;
+  const bool copy = wbuf != nullptr;  // no copy when the Jacobi input is L of Theta = L Q^H
   for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
     const int aa = e >> 5, cc = e & 31;
     const int a = a0 + aa, c = c0 + cc;
@@ -116,10 +116,12 @@ __global__ void __launch_bounds__(256) k_apply_gate4(StateView v, Op2 op, const 
 #pragma unroll
       for (int q = 0; q < 4; ++q) cfma(acc, G[4 * r + q], x[q]);
       T[(int64_t)(2 * a + (r >> 1)) * N + (r & 1) * Dr + c] = acc;
-      Ts[(r & 1) * 32 + cc][2 * aa + (r >> 1)] = acc;
+      if (copy) Ts[(r & 1) * 32 + cc][2 * aa + (r >> 1)] = acc;
     }
   }
+  if (!copy) return;  // uniform over the CTA
   __syncthreads();
+  cx<R> *W = wbuf + (int64_t)b * tw;
   const int rows = min(32, M - 2 * a0), cols = min(32, Dr - c0);
   for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
     const int jl = e >> 5, il = e & 31;
@@ -458,7 +460,8 @@ cudaError_t split_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
   cudaError_t e;
   {
     dim3 grid((c->ub[l + 2] + 31) / 32, (c->ub[l] + 15) / 16, c->batch);
-    k_apply_gate4<R><<<grid, 256, 0, c->stream>>>(v, op, theta, ths, tb, wb, c->tw);
+    k_apply_gate4<R><<<grid, 256, 0, c->stream>>>(v, op, theta, ths, tb, c->svd_lq ? nullptr : wb,
+                                                   c->tw);
     ++c->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
