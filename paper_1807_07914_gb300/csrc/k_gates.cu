@@ -79,10 +79,12 @@ struct ProbTheta {
 };
 
 // Theta = G X on the physical pair; writes theta_buf (in place) and, unless
-// wbuf is null, the column-major Jacobi copy in w_buf. A CTA takes a in [a0, a0+16) and c in
-// [c0, c0+32), i.e. Theta rows 2a0..2a0+31 and columns c0.. and Dr+c0.. of
-// both physical halves: the row-major result goes back along rows, and W is
-// written column by column from a shared-memory transpose of the tile.
+// wbuf is null, the column-major Jacobi copy in w_buf. A CTA takes a in
+// [a0, a0+16) and every column tile c in [c0, c0+32), i.e. Theta rows
+// 2a0..2a0+31 and columns c0.. and Dr+c0.. of both physical halves (the gate,
+// built in FP64 from the state's angles, once per CTA): the row-major result
+// goes back along rows, and W is written column by column from a
+// shared-memory transpose of the tile.
 template <typename R>
 __global__ void __launch_bounds__(256) k_apply_gate4(StateView v, Op2 op, const double *theta,
                                                            int64_t ths, cx<R> *tbuf, cx<R> *wbuf,
@@ -90,44 +92,47 @@ __global__ void __launch_bounds__(256) k_apply_gate4(StateView v, Op2 op, const 
   const int b = blockIdx.z;
   __shared__ cx<R> G[16];
   __shared__ cx<R> Ts[64][33];  // [column s2*32 + cc][row 2*aa + s1]
+  const int l = op.l;
+  const int Dl = dimv(v, b, l), Dr = dimv(v, b, l + 2);
+  const int a0 = blockIdx.y * 16;
+  if (a0 >= Dl) return;  // uniform over the CTA
   if (threadIdx.x == 0) {
     cx<double> Gd[16];
     op2_matrix(op, theta ? theta + (int64_t)b * ths : nullptr, Gd);
     for (int e = 0; e < 16; ++e) G[e] = mkc<R>((R)Gd[e].re, (R)Gd[e].im);
   }
   __syncthreads();
-  const int l = op.l;
-  const int Dl = dimv(v, b, l), Dr = dimv(v, b, l + 2);
-  const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 32;
-  if (a0 >= Dl || c0 >= Dr) return;  // uniform over the CTA
   const int M = 2 * Dl, N = 2 * Dr;
   cx<R> *T = tbuf + (int64_t)b * tw;
   const bool copy = wbuf != nullptr;  // no copy when the Jacobi input is L of Theta = L Q^H
-  for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
-    const int aa = e >> 5, cc = e & 31;
-    const int a = a0 + aa, c = c0 + cc;
-    if (a >= Dl || c >= Dr) continue;
-    cx<R> x[4];
+  for (int c0 = 0; c0 < Dr; c0 += 32) {
+    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
+      const int aa = e >> 5, cc = e & 31;
+      const int a = a0 + aa, c = c0 + cc;
+      if (a >= Dl || c >= Dr) continue;
+      cx<R> x[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = T[(int64_t)(2 * a + (q >> 1)) * N + (q & 1) * Dr + c];
+      for (int q = 0; q < 4; ++q) x[q] = T[(int64_t)(2 * a + (q >> 1)) * N + (q & 1) * Dr + c];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      cx<R> acc = mkc<R>(0, 0);
+      for (int r = 0; r < 4; ++r) {
+        cx<R> acc = mkc<R>(0, 0);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cfma(acc, G[4 * r + q], x[q]);
-      T[(int64_t)(2 * a + (r >> 1)) * N + (r & 1) * Dr + c] = acc;
-      if (copy) Ts[(r & 1) * 32 + cc][2 * aa + (r >> 1)] = acc;
+        for (int q = 0; q < 4; ++q) cfma(acc, G[4 * r + q], x[q]);
+        T[(int64_t)(2 * a + (r >> 1)) * N + (r & 1) * Dr + c] = acc;
+        if (copy) Ts[(r & 1) * 32 + cc][2 * aa + (r >> 1)] = acc;
+      }
     }
-  }
-  if (!copy) return;  // uniform over the CTA
-  __syncthreads();
-  cx<R> *W = wbuf + (int64_t)b * tw;
-  const int rows = min(32, M - 2 * a0), cols = min(32, Dr - c0);
-  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
-    const int jl = e >> 5, il = e & 31;
-    const int s2 = jl >> 5, cc = jl & 31;
-    if (il < rows && cc < cols)
-      W[(int64_t)(s2 * Dr + c0 + cc) * M + 2 * a0 + il] = Ts[jl][il];
+    if (!copy) continue;  // uniform over the CTA
+    __syncthreads();
+    cx<R> *W = wbuf + (int64_t)b * tw;
+    const int rows = min(32, M - 2 * a0), cols = min(32, Dr - c0);
+    for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+      const int jl = e >> 5, il = e & 31;
+      const int s2 = jl >> 5, cc = jl & 31;
+      if (il < rows && cc < cols)
+        W[(int64_t)(s2 * Dr + c0 + cc) * M + 2 * a0 + il] = Ts[jl][il];
+    }
+    __syncthreads();  // Ts is refilled by the next column tile
   }
 }
 
@@ -459,7 +464,7 @@ cudaError_t split_impl(tnmps_ctx *c, const Op2 &op, const double *theta, int64_t
   cx<R> *wb = reinterpret_cast<cx<R> *>(c->w_buf);
   cudaError_t e;
   {
-    dim3 grid((c->ub[l + 2] + 31) / 32, (c->ub[l] + 15) / 16, c->batch);
+    dim3 grid(1, (c->ub[l] + 15) / 16, c->batch);  // a CTA loops over the column tiles
     k_apply_gate4<R><<<grid, 256, 0, c->stream>>>(v, op, theta, ths, tb, c->svd_lq ? nullptr : wb,
                                                    c->tw);
     ++c->launches;
