@@ -405,70 +405,105 @@ __device__ void apply_block_reflector(cx<R> *X, int ldx, int k0, int k1, const c
 
 // householder_qr with panels of NB reflectors: each panel is factored with
 // the reflector-at-a-time loop restricted to its own columns, then its block
-// reflector updates the trailing columns once. Same output as householder_qr.
-// The panel (rows j0..m-1 of its nb columns) is factored in shared memory, in
-// Vs (panel column k, row i at Vs[k * VLD + i - j0]), written back to W once,
-// and then turned in place into the staged reflectors of the trailing update.
+// reflector updates the trailing columns once. Same factorisation as
+// householder_qr (up to summation order). Panel factorisation: warp w keeps
+// panel column j0 + w in registers (the CTA has at least NB warps); warp k
+// forms reflector j0 + k from its column with a warp reduction and writes it
+// as column k of the staged panel Vs (0 above its row, 1 on it, the scaled
+// column below), and after one barrier the warps of the later columns apply it
+// in registers. The factored columns then go back to W, and Vs is already the
+// staged panel of the trailing update.
 template <typename R, int NB, int HR>
 __device__ void householder_qr_blocked(cx<R> *W, int m, int n, cx<R> *tau, R *red, cx<R> *vs,
                                        cx<R> *Ts, cx<R> *Gs, cx<R> *Vs) {
   constexpr int VLD = 32 * HR;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = m < n ? m : n;
   for (int j0 = 0; j0 < r; j0 += NB) {
     const int nb = r - j0 < NB ? r - j0 : NB;
-    const int rows = m - j0;
-    for (int e = threadIdx.x; e < nb * VLD; e += blockDim.x) {
-      const int k = e / VLD, ii = e - k * VLD;
-      if (ii < rows) Vs[e] = W[(int64_t)(j0 + k) * m + j0 + ii];
+    const bool own = warp < nb;
+    const int jc = j0 + warp;  // this warp's panel column
+    cx<R> xr[HR];              // rows j0 + lane + 32 h
+#pragma unroll
+    for (int h = 0; h < HR; ++h) {
+      const int i = j0 + lane + 32 * h;
+      xr[h] = (own && i < m) ? W[(int64_t)jc * m + i] : mkc<R>(0, 0);
     }
-    __syncthreads();
-    for (int j = j0; j < j0 + nb; ++j) {
-      cx<R> *col = Vs + (j - j0) * VLD;  // row i at col[i - j0]
-      R part = 0;
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
-        part += col[i - j0].re * col[i - j0].re + col[i - j0].im * col[i - j0].im;
-      const R xn2 = block_sum(part, red);
-      const cx<R> alpha = col[j - j0];
-      __syncthreads();
-      cx<R> tj = mkc<R>(0, 0);
-      if (!(xn2 == R(0) && alpha.im == R(0))) {
-        const R beta = -copysign(sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2), alpha.re);
-        tj = mkc<R>((beta - alpha.re) / beta, -alpha.im / beta);
-        const R dr = alpha.re - beta, di = alpha.im;
-        const R den = dr * dr + di * di;
-        const cx<R> sc = mkc<R>(dr / den, -di / den);
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-          const cx<R> v = cmul(col[i - j0], sc);
-          col[i - j0] = v;
-          vs[i] = v;
+    for (int k = 0; k < nb; ++k) {
+      const int j = j0 + k;
+      cx<R> *vk = Vs + k * VLD;  // v_j, row i at vk[i - j0]
+      if (warp == k) {
+        R part = 0;
+#pragma unroll
+        for (int h = 0; h < HR; ++h) {
+          const int i = j0 + lane + 32 * h;
+          if (i > j && i < m) part = fma(xr[h].re, xr[h].re, fma(xr[h].im, xr[h].im, part));
         }
-        if (threadIdx.x == 0) {
-          col[j - j0] = mkc<R>(beta, 0);
-          vs[j] = mkc<R>(1, 0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const R xn2 = part;
+        // row j is held by lane k, register 0 (k < NB <= 32)
+        const cx<R> alpha = mkc<R>(__shfl_sync(0xffffffffu, xr[0].re, k),
+                                   __shfl_sync(0xffffffffu, xr[0].im, k));
+        cx<R> tj = mkc<R>(0, 0);
+        if (!(xn2 == R(0) && alpha.im == R(0))) {
+          const R beta =
+              -copysign(sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xn2), alpha.re);
+          tj = mkc<R>((beta - alpha.re) / beta, -alpha.im / beta);
+          const R dr = alpha.re - beta, di = alpha.im;
+          const R den = dr * dr + di * di;
+          const cx<R> sc = mkc<R>(dr / den, -di / den);  // 1 / (alpha - beta)
+#pragma unroll
+          for (int h = 0; h < HR; ++h) {
+            const int i = j0 + lane + 32 * h;
+            if (i > j && i < m) xr[h] = cmul(xr[h], sc);
+          }
+          if (lane == k) xr[0] = mkc<R>(beta, 0);
+        }
+#pragma unroll
+        for (int h = 0; h < HR; ++h) {
+          const int i = j0 + lane + 32 * h;
+          if (i < m) vk[i - j0] = i > j ? xr[h] : mkc<R>(i == j ? R(1) : R(0), R(0));
+        }
+        if (lane == 0) tau[j] = tj;
+      }
+      __syncthreads();
+      const cx<R> tj = tau[j];
+      if (own && warp > k && !(tj.re == R(0) && tj.im == R(0))) {
+        // x <- H_j^H x = x - conj(tau_j) v (v^H x)
+        cx<R> w = mkc<R>(0, 0);
+#pragma unroll
+        for (int h = 0; h < HR; ++h) {
+          const int i = j0 + lane + 32 * h;
+          if (i < m) cfma(w, cconj(vk[i - j0]), xr[h]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+          w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+        }
+        const cx<R> f = cmul(cconj(tj), w);
+#pragma unroll
+        for (int h = 0; h < HR; ++h) {
+          const int i = j0 + lane + 32 * h;
+          if (i < m) {
+            const cx<R> d = cmul(f, vk[i - j0]);
+            xr[h] = mkc<R>(xr[h].re - d.re, xr[h].im - d.im);
+          }
         }
       }
-      if (threadIdx.x == 0) tau[j] = tj;
-      __syncthreads();
-      if ((tj.re == R(0) && tj.im == R(0)) || j + 1 >= j0 + nb) continue;
-      // panel columns j+1..j0+nb-1 (column index relative to the panel)
-      reflect_columns<R, HR>(Vs, VLD, j + 1 - j0, nb, j, m, vs, cconj(tj), j0);
-      __syncthreads();
     }
     // R on and above the diagonal, the reflectors below it
-    for (int e = threadIdx.x; e < nb * VLD; e += blockDim.x) {
-      const int k = e / VLD, ii = e - k * VLD;
-      if (ii < rows) W[(int64_t)(j0 + k) * m + j0 + ii] = Vs[e];
+    if (own) {
+#pragma unroll
+      for (int h = 0; h < HR; ++h) {
+        const int i = j0 + lane + 32 * h;
+        if (i < m) W[(int64_t)jc * m + i] = xr[h];
+      }
     }
+    for (int e = threadIdx.x; e < (NB - nb) * VLD; e += blockDim.x) Vs[nb * VLD + e] = mkc<R>(0, 0);
     __syncthreads();
     if (j0 + nb >= n) continue;
-    // staged reflectors (as stage_panel): explicit 1 on the diagonal, 0 above,
-    // rows >= m and columns >= nb zero
-    for (int e = threadIdx.x; e < NB * VLD; e += blockDim.x) {
-      const int k = e / VLD, ii = e - k * VLD;
-      const cx<R> z = mkc<R>(0, 0);
-      Vs[e] = (k < nb && ii < rows) ? (ii > k ? Vs[e] : (ii == k ? mkc<R>(1, 0) : z)) : z;
-    }
-    __syncthreads();
     block_tfactor<R, NB, VLD>(Vs, j0, nb, m, tau, Ts, Gs);
     apply_block_reflector<R, HR, NB>(W, m, j0 + nb, n, Vs, j0, m, Ts, true);
     __syncthreads();
