@@ -260,9 +260,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": config_dict(args, n, chi, 1, wl["n_params"], len(wl["terms"]), 0),
+        "config": dict(config_dict(args, n, chi, args.batch, wl["n_params"], len(wl["terms"]), 0),
+                       l2="host oracle: the FP64 MPS of one state at a time in host memory"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                         "sample": "per step: 1 theta row, full circuit + all terms"},
+                         "sample": f"per step: 1 of the {args.batch} theta rows of the workload, "
+                                   "full circuit + all terms"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
