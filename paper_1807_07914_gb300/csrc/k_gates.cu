@@ -310,8 +310,8 @@ __global__ void __launch_bounds__(256) k_gate1(StateView v, Op1 op, const double
 // columns stay in registers.
 // Right move at site c: C_c (2Dl x Dr) = Q R;  A_c <- Q;  R stays in w_buf.
 template <typename R, int HR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2) k_qr_right(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
-                                                  int64_t tw, int32_t *newdim) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2)
+    k_qr_right(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf, int64_t tw, int32_t *newdim) {
   const int b = blockIdx.x;
   const int r = gdev::qr_right_cta<R, HR>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
                                       wbuf + (int64_t)b * tw, tbuf + (int64_t)b * tw);
@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2) k_qr_ri
 // Left move at site c: C_c (Dl x 2Dr) = L Q via QR of C_c^H = Q' R';
 // B_c <- Q'^H,  L = R'^H stays (as R') in w_buf.
 template <typename R, int HR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2) k_lq_left(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf,
-                                                 int64_t tw, int32_t *newdim) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2)
+    k_lq_left(StateView v, int c, cx<R> *wbuf, cx<R> *tbuf, int64_t tw, int32_t *newdim) {
   const int b = blockIdx.x;
   const int r = gdev::lq_left_cta<R, HR>(site_ptr<R>(v, b, c), dimv(v, b, c), dimv(v, b, c + 1),
                                      wbuf + (int64_t)b * tw, tbuf + (int64_t)b * tw);
@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2) k_lq_le
 // K3 preconditioner: Theta (theta_buf, row-major 2D_{l-1} x 2D_{l+1}) = L Q^H;
 // L (column-major, the Jacobi input) -> w_buf, Householder scratch in qbuf.
 template <typename R, int HR>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2) k_lq_theta(StateView v, int l, const cx<R> *tbuf,
-                                                  cx<R> *qbuf, cx<R> *wbuf, int64_t tw) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 || HR > 8 ? 1 : 2)
+    k_lq_theta(StateView v, int l, const cx<R> *tbuf, cx<R> *qbuf, cx<R> *wbuf, int64_t tw) {
   const int b = blockIdx.x;
   gdev::lq_theta_cta<R, HR>(tbuf + (int64_t)b * tw, 2 * dimv(v, b, l), 2 * dimv(v, b, l + 2),
                             qbuf + (int64_t)b * tw, wbuf + (int64_t)b * tw);
