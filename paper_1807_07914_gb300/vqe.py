@@ -260,7 +260,7 @@ def compare(wl, starts=3, budget=200000, lr=0.02, ref_lrs=(0.01, 0.03, 0.05, 0.0
     pre = sur.net.get_params().clone()
     mu, sd = sur.mu, sur.sd
     energy = MPSEnergy(*args, dtype, 2 * P + 1, small=1)
-    judge = MPSEnergy(*args, "c128", 8)
+    exact = MPSEnergy(*args, "c128", 8)      # complex128 re-evaluation
     rows = []
     for k in range(starts):
         t2 = time.time()
@@ -272,8 +272,8 @@ def compare(wl, starts=3, budget=200000, lr=0.02, ref_lrs=(0.01, 0.03, 0.05, 0.0
             refs.append(b)
         e_star_run = min(b[0] for b in refs)
         best_ref = min(refs, key=lambda b: b[0])
-        e_star = float(judge(best_ref[1][None])[0])
-        # both compared runs are judged in the optimisers' own form
+        e_star = float(exact(best_ref[1][None])[0])
+        # both compared runs are scored in the optimisers' own form
         target = e_star_run + 1e-4
         energy.evals = 0
         hp, bp = plain_adam(energy, theta0, lr, budget)
@@ -282,12 +282,12 @@ def compare(wl, starts=3, budget=200000, lr=0.02, ref_lrs=(0.01, 0.03, 0.05, 0.0
         sur.X, sur.Y = X.copy(), Y.copy()
         energy.evals = 0
         hs, bs, st = surrogate_adam(energy, sur, theta0, lr, budget, rng=np.random.default_rng(k))
-        row = {"start": k, "E0": float(judge(theta0[None])[0]), "E_star": e_star,
+        row = {"start": k, "E0": float(exact(theta0[None])[0]), "E_star": e_star,
                "E_star_optimiser_form": e_star_run,
                "reference_bests": [float(b[0]) for b in refs],
                "plain_best": float(bp[0]), "surrogate_best": float(bs[0]),
-               "plain_best_c128": float(judge(bp[1][None])[0]),
-               "surrogate_best_c128": float(judge(np.asarray(bs[1])[None])[0]),
+               "plain_best_c128": float(exact(bp[1][None])[0]),
+               "surrogate_best_c128": float(exact(np.asarray(bs[1])[None])[0]),
                "plain_evals_to_target": evals_to(hp, target),
                "surrogate_evals_to_target": evals_to(hs, target),
                "plain_evals_to_plain_best": evals_to(hp, bp[0]),
